@@ -1,0 +1,377 @@
+"""Benchmark: exact Euclidean clustering throughput on one GB300 per rank.
+
+Default workload: the accumulated 64-beam LiDAR corridor map (~27.9M points,
+d = 0.2 m, min 100, max 2,000,000), seeded and synthetic.  A step is one call
+of fec_cluster over the whole cloud (every stage of the pipeline: quantise,
+grid keys, radix sort, cell table, neighbour test + union, flatten, size
+filter, relabel).  The input (335 MB of xyz) is larger than the 126 MB L2, so
+no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded crop of the same map.
+
+Multi-GPU (torchrun): one process per GPU, each clustering its own replica of
+the map (independent clouds, no collective on the data path); value = points
+of all ranks / max over ranks of the step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s clustered (27M cloud, 120k frame); batched frames/s; serve p50/p99 ms"
+UNIT = "Mpoints/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic DRAM bytes of one launch of each kernel, per unit it processes
+# (n = points, Ms = sub-cells, Mc = cells); compulsory traffic only.
+KERNEL_BYTES = {
+    "k_bbox": lambda n, Ms, Mc: 12 * n,
+    "k_keys_u32": lambda n, Ms, Mc: 16 * n,
+    "onesweep_u32": lambda n, Ms, Mc: 16 * n,
+    "k_cells_u32": lambda n, Ms, Mc: 40 * n + 4 * Ms + 12 * Mc,
+    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 56 * Ms,
+    "k_union": lambda n, Ms, Mc: 12 * Mc + 40 * Ms,
+    "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
+    "k_labels": lambda n, Ms, Mc: 12 * n,
+}
+KERNEL_SOURCE = {
+    "k_bbox": "fec_grid.cu", "k_keys_u32": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
+    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_union": "fec_union.cu",
+    "k_flatten_stats": "fec_union.cu", "k_labels": "fec_union.cu",
+}
+HOUSEKEEPING = ("memset", "h2d", "d2h", "summary")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(fname):
+    p = os.path.join(ROOT, "paper_2208_07678_gb300", "csrc", fname)
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel's source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    e = j.get(workload, {}).get(kernel)
+    if not e or e.get("source_sha") != source_hash(KERNEL_SOURCE.get(kernel, "fec_api.cu")):
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(name):
+    from paper_2208_07678_gb300 import synth
+
+    if name == "map_27m":
+        return synth.map_27m()
+    if name == "frame_120k":
+        return synth.frame_120k()
+    if name == "blobs_20k":
+        return synth.blobs_20k()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def oracle_sample(cloud, target_points):
+    """A bounded, density-preserving sample of the workload for the oracle:
+    the map's points inside an x-window (whole cloud if it is small)."""
+    from paper_2208_07678_gb300 import synth
+
+    if cloud.n <= target_points:
+        return cloud, f"whole cloud, n={cloud.n}"
+    xs = np.sort(cloud.xyz[::97, 0])
+    mid = float(np.median(xs))
+    width = (xs[-1] - xs[0]) * target_points / cloud.n
+    crop = synth.map_crop(cloud, mid - width / 2, mid + width / 2)
+    return crop, f"x-window crop of {cloud.name}: x in [{mid - width / 2:.1f}, {mid + width / 2:.1f}) m, n={crop.n}"
+
+
+def time_oracle(cloud, target_points):
+    import oracle
+
+    sample, desc = oracle_sample(cloud, target_points)
+    t0 = time.perf_counter()
+    oracle.cluster(sample.xyz, sample.d, sample.min_size, sample.max_size)
+    dt = time.perf_counter() - t0
+    return sample.n / dt / 1e6, desc, sample.n, dt
+
+
+def dist_setup(backend):
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device=None):
+    """MAX of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def run_reference(args):
+    world, rank, _ = env_int("WORLD_SIZE", 1), env_int("RANK", 0), 0
+    if rank != 0:
+        return 0
+    cloud = make_workload(args.workload)
+    target = args.ref_points
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, _, _ = time_oracle(cloud, target)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": cloud.n, "d": cloud.d, "min_size": cloud.min_size,
+                   "max_size": cloud.max_size, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2208_07678_gb300 import build as libbuild
+    from paper_2208_07678_gb300 import fec
+
+    libbuild.build()
+    cloud = make_workload(args.workload)
+    n = cloud.n
+    stream = torch.cuda.current_stream(dev)
+    ctx = fec.Context(device=local, cuda_stream=stream.cuda_stream)
+    xyz_dev = torch.from_numpy(cloud.xyz).to(dev)
+    lab_dev = torch.empty(n, dtype=torch.int32, device=dev)
+    xyz_host = torch.from_numpy(cloud.xyz).pin_memory()
+    lab_host = torch.empty(n, dtype=torch.int32).pin_memory()
+
+    def step_dev():
+        return ctx.cluster(xyz_dev, cloud.d, cloud.min_size, cloud.max_size, labels=lab_dev)[1]
+
+    def step_e2e():
+        return ctx.cluster(xyz_host, cloud.d, cloud.min_size, cloud.max_size, labels=lab_host)[1]
+
+    def timed(fn, steps):
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return e0.elapsed_time(e1) / steps
+
+    for _ in range(args.warmup):
+        k = step_dev()
+    with ClockSampler(local) as clocks:
+        ms_dev = timed(step_dev, args.steps)
+        # traced pass: per-kernel device time with CUDA events on the same stream
+        ctx.trace(True)
+        ms_traced = timed(step_dev, args.steps)
+        trace = ctx.trace_read()
+        ctx.trace(False)
+        for _ in range(max(1, args.warmup // 2)):
+            step_e2e()
+        ms_e2e = timed(step_e2e, args.steps)
+    clk = clocks.summary()
+    stats = ctx.stats()
+    ms_dev_max = max_over_ranks(ms_dev, world, dev)
+    ms_e2e_max = max_over_ranks(ms_e2e, world, dev)
+    value = world * n / (ms_dev_max * 1e-3) / 1e6
+    e2e_value = world * n / (ms_e2e_max * 1e-3) / 1e6
+
+    # dominant kernel of the traced pass
+    kernels = [t for t in trace if not t["name"].startswith(HOUSEKEEPING)]
+    launches_per_step = sum(t["launches"] for t in kernels) / args.steps
+    dom = max(kernels, key=lambda t: t["total_ms"])
+    Ms, Mc = stats["subcells"], stats["cells"]
+    peak, peak_kind = load_peaks()
+    roof = None
+    if dom["name"] in KERNEL_BYTES:
+        per_launch_ms = dom["total_ms"] / dom["launches"]
+        alg = KERNEL_BYTES[dom["name"]](n, Ms, Mc)
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(dom["name"], args.workload),
+                "alg_bytes_per_launch": alg, "ms_per_launch": per_launch_ms}
+    step_total_ms = sum(t["total_ms"] for t in trace) / args.steps
+    breakdown = {t["name"]: round(t["total_ms"] / args.steps, 4) for t in
+                 sorted(trace, key=lambda t: -t["total_ms"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, sn, dt = time_oracle(cloud, args.cpu_points)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(dt, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_dev_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": cloud.d, "min_size": cloud.min_size,
+                       "max_size": cloud.max_size, "num_clusters": int(k), "cells": Mc,
+                       "subcells": Ms, "l2": "input 335 MB > 126 MB L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": ms_e2e_max,
+                    "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * n + 4},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "trace_ms_per_step": {"total": round(step_total_ms, 4), "traced_step_ms": ms_traced,
+                                  "by_kernel": breakdown},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="map_27m")
+    ap.add_argument("--cpu-points", type=int, default=4_000_000,
+                    help="oracle sample size for cpu_baseline (about 10-30 s of CPU work)")
+    ap.add_argument("--ref-points", type=int, default=1_000_000,
+                    help="oracle sample size per step of --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * fec.h -- C ABI of the GB300 exact Euclidean clustering library (FEC,
+ * "Fast Euclidean Clustering for Point Cloud Segmentation", arxiv 2208.07678).
+ *
+ * The library labels every point of an unorganised 3-D cloud with the
+ * connected component of the graph that joins two points when their
+ * Euclidean distance is at most d (Eq. 1, Section 2.2), drops components
+ * whose size lies outside [min_size, max_size] (the size bounds shared with
+ * PCL's Euclidean cluster extraction, Section 3.1; Algorithm 1's Th_max is
+ * read as max_size), and numbers the kept components 0..k-1 in increasing
+ * order of their smallest point index.  Dropped points get label -1.
+ *
+ * Exactness.  Coordinates are quantised to integer units of 1/1024 m,
+ * q = rint(x * 1024) (round half to even), and two points join iff
+ * dx^2 + dy^2 + dz^2 <= T2 with T2 = floor((d * 1024)^2) computed in double.
+ * The result is unique, so labels are bit-identical run to run and to any
+ * correct implementation of the same definition.
+ *
+ * Limits.  0 <= n <= FEC_MAX_POINTS.  |q| < 2^23 on every axis (|x| < 8192 m).
+ * d finite and > 0.  0 <= min_size <= max_size (INT64_MAX = unbounded).  The
+ * uniform grid with cell side about d over the cloud's bounding box must be
+ * addressable with a 61-bit cell key (always true for d >= 0.5 mm over an
+ * 8 km cube); otherwise FEC_ERR_OUT_OF_RANGE.
+ *
+ * Memory.  Every buffer passed in is owned by the caller.  A context owns its
+ * device workspace and grows it on demand within mem_budget_bytes.  Pointers
+ * may be host or device memory (detected per call with
+ * cudaPointerGetAttributes); host buffers are staged through the context.
+ *
+ * Errors.  No call throws or aborts.  On an error the outputs are unspecified
+ * and nothing leaks.  A CUDA error leaves the context usable only if the
+ * device context itself survived.
+ */
+#ifndef FEC_H
+#define FEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEC_MAX_POINTS ((int64_t)1 << 30)
+
+typedef enum {
+    FEC_OK = 0,
+    FEC_ERR_INVALID_ARG = 1,    /* bad pointer, n, d, or size bounds */
+    FEC_ERR_NONFINITE = 2,      /* a coordinate is NaN or +-Inf */
+    FEC_ERR_OUT_OF_RANGE = 3,   /* |rint(x*1024)| >= 2^23, or grid key > 61 bits */
+    FEC_ERR_OOM = 4,            /* workspace above mem_budget_bytes, or cudaMalloc failed */
+    FEC_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    FEC_ERR_NOT_CONVERGED = 6,  /* a bounded device loop hit its iteration cap */
+    FEC_ERR_NOT_READY = 7,      /* fec_serve_poll: request still running */
+    FEC_ERR_BUSY = 8,           /* fec_serve_submit: request can never fit the budget / queue full */
+    FEC_ERR_TIMEOUT = 9         /* fec_serve_poll: the wait ended before completion */
+} fec_status;
+
+typedef struct fec_ctx fec_ctx;
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    size_t mem_budget_bytes;  /* cap on device workspace; 0 = no cap */
+    void *cuda_stream;        /* cudaStream_t to run on; NULL = a stream owned by the context */
+    const char *autotune_cache; /* path of the batch tuner's cache file; NULL = in memory only */
+} fec_options;
+
+/* Per-call counters of the last fec_cluster / fec_cluster_batch call. */
+typedef struct {
+    int64_t n;                /* points */
+    int64_t cells;            /* occupied grid cells (side S = 2h units) */
+    int64_t subcells;         /* occupied sub-cells (side h units; each is a clique) */
+    int64_t num_clusters;     /* kept clusters */
+    int64_t key_bits;         /* bits of the sort key actually used */
+    int64_t workspace_bytes;  /* device workspace held by the context */
+    int32_t R;                /* floor(sqrt(T2)): largest joined offset per axis, units */
+    int32_t h;                /* sub-cell side, units */
+    int64_t T2;               /* squared join radius, units^2 */
+} fec_stats;
+
+/* Create a context on options->device (options may be NULL: device 0, no
+ * budget, own stream).  *out receives the context.  Thread-compatible: one
+ * thread at a time per context for fec_cluster / fec_cluster_batch. */
+fec_status fec_create(const fec_options *options, fec_ctx **out);
+
+/* Destroy a context; waits for its serving requests and frees everything.
+ * NULL is a no-op. */
+void fec_destroy(fec_ctx *ctx);
+
+/* Cluster one cloud (Eq. 1; Algorithm 1's input and output).
+ *   xyz          float32 [n][3], x y z interleaved, host or device memory.
+ *   n            number of points, 0 <= n <= FEC_MAX_POINTS.
+ *   d            join radius in metres (distance <= d joins), finite, > 0.
+ *   min_size, max_size  inclusive size bounds of kept clusters.
+ *   labels       int32 [n], host or device memory, written in input order:
+ *                0..k-1 by smallest point index, -1 for dropped points.
+ *   num_clusters host int32: k, the number of kept clusters.
+ * Synchronous: returns after labels and num_clusters are written.
+ * Precedence of data errors: NONFINITE before OUT_OF_RANGE. */
+fec_status fec_cluster(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                       int64_t max_size, int32_t *labels, int32_t *num_clusters);
+
+/* Cluster nb independent frames in one device pass (frames of uneven size,
+ * per-frame d and size bounds).  Frame f holds points offsets[f] ..
+ * offsets[f+1]-1 of the concatenated xyz.  Labels are frame-local (each frame
+ * numbered 0..k_f-1 exactly as fec_cluster would number it alone).
+ *   xyz          float32 [offsets[nb]][3], host or device.
+ *   offsets      host int64 [nb+1], offsets[0] = 0, non-decreasing.
+ *   d, min_size, max_size  host arrays [nb].
+ *   labels       int32 [offsets[nb]], host or device.
+ *   num_clusters host int32 [nb].
+ * Same exactness and error rules as fec_cluster; a data error in any frame
+ * fails the whole call. */
+fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offsets, int32_t nb,
+                             const float *d, const int64_t *min_size, const int64_t *max_size,
+                             int32_t *labels, int32_t *num_clusters);
+
+/* Serving: submit one request.  The input is copied before the call returns;
+ * labels_out (host memory, int32 [n]) must stay valid until fec_serve_poll
+ * returns a final status for the ticket.  Requests run concurrently on the
+ * context's device as workspace slots and the memory budget allow
+ * (continuous batching); each result equals fec_cluster on that request
+ * alone.  FEC_ERR_BUSY if the request alone exceeds the budget.
+ * Thread-safe. */
+fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                            int64_t max_size, int32_t *labels_out, uint64_t *ticket);
+
+/* Serving: wait up to timeout_ms (0 = just check, <0 = forever) for a ticket.
+ * FEC_OK: labels_out and *num_clusters are final and the ticket is released.
+ * FEC_ERR_NOT_READY (timeout_ms == 0) or FEC_ERR_TIMEOUT (the wait of
+ * timeout_ms > 0 ended first): still queued or running; the ticket stays
+ * valid.  FEC_ERR_INVALID_ARG: unknown ticket.  Any other status is the
+ * request's final error and releases the ticket.  Thread-safe. */
+fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, int timeout_ms);
+
+/* Counters of the last fec_cluster / fec_cluster_batch call on ctx. */
+fec_status fec_get_stats(const fec_ctx *ctx, fec_stats *out);
+
+/* Tracing: per-kernel device time, measured with CUDA events recorded on
+ * the context's stream after every launch of fec_cluster /
+ * fec_cluster_batch while enabled.  The time charged to a launch is the
+ * interval since the previous event on the stream (the launch itself plus any
+ * idle gap before it).  Enabling clears the accumulators. */
+typedef struct {
+    const char *name;    /* kernel or copy name (static string) */
+    int64_t launches;    /* launches recorded */
+    double total_ms;     /* summed device time */
+} fec_trace_entry;
+
+fec_status fec_trace_enable(fec_ctx *ctx, int enable);
+
+/* Copy up to cap accumulated entries into out (out may be NULL to count);
+ * returns the number of distinct names, or -1 on a bad argument. */
+int fec_trace_read(const fec_ctx *ctx, fec_trace_entry *out, int cap);
+
+/* Device workspace bytes fec_cluster needs for n points at radius d. */
+int64_t fec_workspace_bytes(int64_t n, float d);
+
+/* Static string naming a status. */
+const char *fec_status_string(fec_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEC_H */

@@ -1,0 +1,560 @@
+// fec_api.cu -- contexts, workspace, the one-cloud pipeline on a stream, and
+// the C ABI declared in include/fec.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fec.h"
+#include "fec_internal.cuh"
+#include "fec_serve.h"
+
+namespace fec {
+
+// ---------------------------------------------------------------------------
+// Parameters
+// ---------------------------------------------------------------------------
+
+Params make_params(uint32_t n, float d)
+{
+    Params p{};
+    p.n = n;
+    // T2 = floor((d*1024)^2); any two valid points are closer than
+    // sqrt(3) * 2^24 units, so clamping T2 at 3 * 2^48 changes no decision.
+    const double s = (double)d * 1024.0;
+    double t = std::floor(s * s);
+    const double cap = 3.0 * 281474976710656.0;
+    if (t > cap) t = cap;
+    p.T2 = (int64_t)t;
+    int64_t R = (int64_t)std::sqrt((double)p.T2);
+    while (R * R > p.T2) --R;
+    while ((R + 1) * (R + 1) <= p.T2) ++R;
+    p.R = (int32_t)R;
+    int64_t h = (R + 1) / 2;
+    if (h < 1) h = 1;
+    if (h > (1 << 24)) h = 1 << 24;
+    p.h = (int32_t)h;
+    p.S = (int32_t)(2 * h);
+    p.slab_cap = (uint32_t)(((1u << 24) - 1) / (uint32_t)p.S + 2);
+    return p;
+}
+
+static int bitlen_host(uint64_t v)
+{
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+int max_sort_passes(const Params &prm)
+{
+    const int b = bitlen_host(((1u << 24) - 1) / (uint32_t)prm.S);
+    int bits = 3 * b + 3;
+    if (bits > 64) bits = 64;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+int kept_sort_passes(uint32_t n)
+{
+    const int b = n > 1 ? bitlen_host(n - 1) : 0;
+    return (b + kRadixBits - 1) / kRadixBits;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+
+size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? (void *)((char *)base + off) : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t n = cap_n;
+    ws.plan = (Plan *)take(sizeof(Plan));
+    ws.xyz = (float *)take(12 * n);
+    ws.labels = (int32_t *)take(4 * n);
+    ws.keys_a = take(8 * n);
+    ws.keys_b = take(8 * n);
+    ws.vals_a = (uint32_t *)take(4 * n);
+    ws.vals_b = (uint32_t *)take(4 * n);
+    ws.sort_status = (uint32_t *)take(4 * sort_status_words((uint32_t)n));
+    ws.scan_status = (unsigned long long *)take(8 * (n / kScanTile + 2));
+    ws.rec = (Rec *)take(sizeof(Rec) * n);
+    ws.sc_of = (uint32_t *)take(4 * n);
+    ws.sc_start = (uint32_t *)take(4 * (n + 2));
+    ws.box = (SubBox *)take(sizeof(SubBox) * n);
+    ws.sminidx = (uint32_t *)take(4 * n);
+    ws.parent = (uint32_t *)take(4 * n);
+    ws.csize = (uint32_t *)take(4 * n);
+    ws.cmin = (uint32_t *)take(4 * n);
+    ws.crank = (int32_t *)take(4 * n);
+    ws.big = (uint32_t *)take(4 * n);
+    ws.cell_key = (unsigned long long *)take(8 * n);
+    ws.cell_sc = (uint32_t *)take(4 * (n + 2));
+    ws.slab_lo = (uint32_t *)take(4 * (size_t)slab_cap);
+    ws.slab_hi = (uint32_t *)take(4 * (size_t)slab_cap);
+    off = (off + 255) & ~(size_t)255;
+    if (base) {
+        ws.base = base;
+        ws.bytes = off;
+        ws.cap_n = cap_n;
+        ws.slab_cap = slab_cap;
+    }
+    return off;
+}
+
+// ---------------------------------------------------------------------------
+// Pipeline
+// ---------------------------------------------------------------------------
+
+cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
+                            long long min_size, long long max_size, int32_t *labels,
+                            cudaStream_t st)
+{
+    const Params prm = make_params(n, d);
+    const int sort_grid = ws.sms * 2;
+    cudaError_t e = enqueue_front(ws, xyz, prm, st);
+    if (e != cudaSuccess) return e;
+    // a2: both key widths are enqueued; the plan enables one of them.
+    e = launch_sort_u32(ws, "onesweep_u32", &ws.plan->sort, (uint32_t *)ws.keys_a, ws.vals_a,
+                        (uint32_t *)ws.keys_b, ws.vals_b, true, ws.sort_status, n, 4, sort_grid, st,
+                        &ws.plan->status);
+    if (e != cudaSuccess) return e;
+    const int p64 = max_sort_passes(prm);
+    if (p64 > 4) {
+        e = launch_sort_u64(ws, "onesweep_u64", &ws.plan->sort, (unsigned long long *)ws.keys_a,
+                            ws.vals_a,
+                            (unsigned long long *)ws.keys_b, ws.vals_b, true, ws.sort_status, n,
+                            p64, sort_grid, st, &ws.plan->status);
+        if (e != cudaSuccess) return e;
+    }
+    e = enqueue_cells(ws, xyz, prm, st);
+    if (e != cudaSuccess) return e;
+    e = enqueue_union(ws, prm, min_size, max_size, st);
+    if (e != cudaSuccess) return e;
+    const int kp = kept_sort_passes(n);
+    if (kp > 0) {
+        e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), ws.sms * 4, st);
+        if (e != cudaSuccess) return e;
+        FEC_MARK(ws, "hist_kept", st);
+        e = launch_sort_u32(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
+                            ws.kept_key_b(),
+                            ws.kept_val_b(), false, ws.sort_status, n, kp, sort_grid, st,
+                            &ws.plan->status);
+        if (e != cudaSuccess) return e;
+    }
+    return enqueue_labels(ws, labels, st);
+}
+
+// Small summary of a finished call, packed on the device for one copy.
+struct Summary {
+    uint32_t status, k, M_s, M_c, key_bits, pad[3];
+};
+
+__global__ void k_summary(const Plan *plan, Summary *out)
+{
+    if (threadIdx.x == 0) {
+        out->status = plan->status;
+        out->k = plan->kept.n;
+        out->M_s = plan->M_s;
+        out->M_c = plan->M_c;
+        out->key_bits = plan->key_bits;
+    }
+}
+
+fec_status status_from_bits(uint32_t s)
+{
+    if (s & ST_NONFINITE) return FEC_ERR_NONFINITE;
+    if (s & (ST_OUT_OF_RANGE | ST_KEY_OVERFLOW)) return FEC_ERR_OUT_OF_RANGE;
+    if (s & (ST_WAIT_TIMEOUT | ST_UNION_CAP)) return FEC_ERR_NOT_CONVERGED;
+    if (s & ST_SIZE_OVERFLOW) return FEC_ERR_OUT_OF_RANGE;
+    return FEC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tracing
+// ---------------------------------------------------------------------------
+
+struct Trace {
+    cudaEvent_t start = nullptr;
+    std::vector<cudaEvent_t> pool;
+    std::vector<const char *> names;
+    int used = 0;
+    struct Acc {
+        const char *name;
+        int64_t launches;
+        double ms;
+    };
+    std::vector<Acc> acc;
+
+    bool init(int n)
+    {
+        if (start) return true;
+        if (cudaEventCreate(&start) != cudaSuccess) return false;
+        pool.resize(n);
+        names.resize(n);
+        for (auto &e : pool)
+            if (cudaEventCreate(&e) != cudaSuccess) return false;
+        return true;
+    }
+    void destroy()
+    {
+        if (start) cudaEventDestroy(start);
+        for (auto &e : pool)
+            if (e) cudaEventDestroy(e);
+        start = nullptr;
+        pool.clear();
+    }
+    void begin(cudaStream_t st)
+    {
+        used = 0;
+        cudaEventRecord(start, st);
+    }
+    // after the stream has been synchronised
+    void end()
+    {
+        cudaEvent_t prev = start;
+        for (int i = 0; i < used; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, prev, pool[i]);
+            prev = pool[i];
+            bool hit = false;
+            for (auto &a : acc)
+                if (a.name == names[i] || std::strcmp(a.name, names[i]) == 0) {
+                    a.launches += 1;
+                    a.ms += ms;
+                    hit = true;
+                    break;
+                }
+            if (!hit) acc.push_back({names[i], 1, (double)ms});
+        }
+        used = 0;
+    }
+};
+
+void trace_mark(const Workspace &ws, const char *name, cudaStream_t st)
+{
+    Trace *t = ws.trace;
+    if (!t || t->used >= (int)t->pool.size()) return;
+    cudaEventRecord(t->pool[t->used], st);
+    t->names[t->used] = name;
+    ++t->used;
+}
+
+int sm_count()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+}  // namespace fec
+
+using namespace fec;
+
+struct fec_ctx {
+    int device = 0;
+    size_t budget = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Workspace ws;
+    Summary *summary_dev = nullptr;
+    Summary *summary_host = nullptr;  // pinned
+    fec_stats last{};
+    std::mutex mu;
+    ServeEngine *serve = nullptr;
+    Trace trace;
+    bool tracing = false;
+};
+
+namespace {
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+fec_status check_args(int64_t n, float d, int64_t min_size, int64_t max_size)
+{
+    if (n < 0 || n > FEC_MAX_POINTS) return FEC_ERR_INVALID_ARG;
+    if (!std::isfinite(d) || !(d > 0.0f)) return FEC_ERR_INVALID_ARG;
+    if (min_size < 0 || max_size < min_size) return FEC_ERR_INVALID_ARG;
+    return FEC_OK;
+}
+
+// Grow the workspace to hold n points at slab capacity slab_cap.
+fec_status ensure_workspace(fec_ctx *ctx, size_t n, uint32_t slab_cap)
+{
+    Workspace &ws = ctx->ws;
+    if (ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
+    size_t cap = n;
+    if (ws.base && cap < ws.cap_n + ws.cap_n / 4) cap = ws.cap_n + ws.cap_n / 4;
+    if (cap < 4096) cap = 4096;
+    uint32_t sc = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
+    Workspace probe;
+    size_t bytes = workspace_layout(probe, nullptr, cap, sc);
+    if (ctx->budget && bytes > ctx->budget) {
+        cap = n;  // retry without headroom
+        bytes = workspace_layout(probe, nullptr, cap, sc);
+        if (bytes > ctx->budget) return FEC_ERR_OOM;
+    }
+    if (ws.base) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ws.base);
+        ws.base = nullptr;
+        ws.cap_n = 0;
+    }
+    void *base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FEC_ERR_OOM;
+    }
+    workspace_layout(ws, base, cap, sc);
+    return FEC_OK;
+}
+
+fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clusters)
+{
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return FEC_ERR_CUDA;
+    const Summary &s = *ctx->summary_host;
+    fec_stats &st = ctx->last;
+    st.n = n;
+    st.cells = s.M_c;
+    st.subcells = s.M_s;
+    st.num_clusters = s.k;
+    st.key_bits = s.key_bits;
+    st.workspace_bytes = (int64_t)ctx->ws.bytes;
+    st.R = prm.R;
+    st.h = prm.h;
+    st.T2 = prm.T2;
+    const fec_status f = status_from_bits(s.status);
+    if (f == FEC_OK && num_clusters) *num_clusters = (int32_t)s.k;
+    return f;
+}
+
+}  // namespace
+
+namespace fec {
+
+// One cloud on the context's stream; device or host pointers.  Caller holds ctx->mu.
+fec_status cluster_locked(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                          int64_t max_size, int32_t *labels, int32_t *num_clusters)
+{
+    const Params prm = make_params((uint32_t)n, d);
+    fec_status s = ensure_workspace(ctx, (size_t)n, prm.slab_cap);
+    if (s != FEC_OK) return s;
+    Workspace &ws = ctx->ws;
+    ws.trace = ctx->tracing ? &ctx->trace : nullptr;
+    if (ws.trace) ws.trace->begin(ctx->stream);
+    const float *xin = xyz;
+    if (!is_device_ptr(xyz)) {
+        if (cudaMemcpyAsync(ws.xyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess)
+            return FEC_ERR_CUDA;
+        FEC_MARK(ws, "h2d_xyz", ctx->stream);
+        xin = ws.xyz;
+    }
+    const bool dev_out = is_device_ptr(labels);
+    int32_t *lout = dev_out ? labels : ws.labels;
+    if (enqueue_cluster(ws, xin, (uint32_t)n, d, min_size, max_size, lout, ctx->stream) !=
+        cudaSuccess)
+        return FEC_ERR_CUDA;
+    if (!dev_out) {
+        if (cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess)
+            return FEC_ERR_CUDA;
+        FEC_MARK(ws, "d2h_labels", ctx->stream);
+    }
+    k_summary<<<1, 32, 0, ctx->stream>>>(ws.plan, ctx->summary_dev);
+    if (cudaMemcpyAsync(ctx->summary_host, ctx->summary_dev, sizeof(Summary),
+                        cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return FEC_ERR_CUDA;
+    FEC_MARK(ws, "summary", ctx->stream);
+    const fec_status st = finish(ctx, n, prm, num_clusters);
+    if (ws.trace) ws.trace->end();
+    ws.trace = nullptr;
+    return st;
+}
+
+size_t ctx_budget(const fec_ctx *ctx) { return ctx->budget; }
+ServeEngine *ctx_serve(fec_ctx *ctx) { return ctx->serve; }
+
+// Frames one after another through the one-cloud pipeline.
+fec_status batch_locked(fec_ctx *ctx, const float *xyz, const int64_t *offsets, int32_t nb,
+                        const float *d, const int64_t *min_size, const int64_t *max_size,
+                        int32_t *labels, int32_t *num_clusters)
+{
+    fec_status worst = FEC_OK;
+    for (int32_t f = 0; f < nb; ++f) {
+        const int64_t n = offsets[f + 1] - offsets[f];
+        num_clusters[f] = 0;
+        if (n == 0) continue;
+        const fec_status s = cluster_locked(ctx, xyz + 3 * offsets[f], n, d[f], min_size[f],
+                                            max_size[f], labels + offsets[f], &num_clusters[f]);
+        if (s != FEC_OK && worst == FEC_OK) worst = s;
+    }
+    return worst;
+}
+
+}  // namespace fec
+
+extern "C" {
+
+const char *fec_status_string(fec_status s)
+{
+    switch (s) {
+    case FEC_OK: return "FEC_OK";
+    case FEC_ERR_INVALID_ARG: return "FEC_ERR_INVALID_ARG";
+    case FEC_ERR_NONFINITE: return "FEC_ERR_NONFINITE";
+    case FEC_ERR_OUT_OF_RANGE: return "FEC_ERR_OUT_OF_RANGE";
+    case FEC_ERR_OOM: return "FEC_ERR_OOM";
+    case FEC_ERR_CUDA: return "FEC_ERR_CUDA";
+    case FEC_ERR_NOT_CONVERGED: return "FEC_ERR_NOT_CONVERGED";
+    case FEC_ERR_NOT_READY: return "FEC_ERR_NOT_READY";
+    case FEC_ERR_BUSY: return "FEC_ERR_BUSY";
+    case FEC_ERR_TIMEOUT: return "FEC_ERR_TIMEOUT";
+    }
+    return "FEC_ERR_UNKNOWN";
+}
+
+int64_t fec_workspace_bytes(int64_t n, float d)
+{
+    if (n < 0 || !std::isfinite(d) || !(d > 0.0f)) return -1;
+    const Params prm = make_params((uint32_t)n, d);
+    Workspace probe;
+    return (int64_t)workspace_layout(probe, nullptr, (size_t)(n < 4096 ? 4096 : n), prm.slab_cap);
+}
+
+fec_status fec_create(const fec_options *opt, fec_ctx **out)
+{
+    if (!out) return FEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    fec_ctx *ctx = new (std::nothrow) fec_ctx();
+    if (!ctx) return FEC_ERR_OOM;
+    ctx->device = opt ? opt->device : 0;
+    ctx->budget = opt ? opt->mem_budget_bytes : 0;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return FEC_ERR_CUDA;
+    }
+    if (opt && opt->cuda_stream) {
+        ctx->stream = (cudaStream_t)opt->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return FEC_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    ctx->ws.device = ctx->device;
+    ctx->ws.sms = sm_count();
+    if (cudaMalloc(&ctx->summary_dev, sizeof(Summary)) != cudaSuccess ||
+        cudaMallocHost(&ctx->summary_host, sizeof(Summary)) != cudaSuccess) {
+        cudaGetLastError();
+        fec_destroy(ctx);
+        return FEC_ERR_OOM;
+    }
+    ctx->serve = serve_create(ctx, opt ? opt->autotune_cache : nullptr);
+    *out = ctx;
+    return FEC_OK;
+}
+
+void fec_destroy(fec_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->serve) serve_destroy(ctx->serve);
+    ctx->trace.destroy();
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->summary_dev) cudaFree(ctx->summary_dev);
+    if (ctx->summary_host) cudaFreeHost(ctx->summary_host);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+fec_status fec_cluster(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                       int64_t max_size, int32_t *labels, int32_t *num_clusters)
+{
+    if (!ctx || !num_clusters) return FEC_ERR_INVALID_ARG;
+    fec_status s = check_args(n, d, min_size, max_size);
+    if (s != FEC_OK) return s;
+    if (n > 0 && (!xyz || !labels)) return FEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEC_ERR_CUDA;
+    if (n == 0) {
+        *num_clusters = 0;
+        ctx->last = fec_stats{};
+        return FEC_OK;
+    }
+    return cluster_locked(ctx, xyz, n, d, min_size, max_size, labels, num_clusters);
+}
+
+fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offsets, int32_t nb,
+                             const float *d, const int64_t *min_size, const int64_t *max_size,
+                             int32_t *labels, int32_t *num_clusters)
+{
+    if (!ctx || nb < 0 || (nb > 0 && (!offsets || !d || !min_size || !max_size || !num_clusters)))
+        return FEC_ERR_INVALID_ARG;
+    if (nb == 0) return FEC_OK;
+    if (offsets[0] != 0) return FEC_ERR_INVALID_ARG;
+    for (int32_t f = 0; f < nb; ++f) {
+        if (offsets[f + 1] < offsets[f]) return FEC_ERR_INVALID_ARG;
+        const fec_status s = check_args(offsets[f + 1] - offsets[f], d[f], min_size[f], max_size[f]);
+        if (s != FEC_OK) return s;
+    }
+    if (offsets[nb] > 0 && (!xyz || !labels)) return FEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEC_ERR_CUDA;
+    return batch_locked(ctx, xyz, offsets, nb, d, min_size, max_size, labels, num_clusters);
+}
+
+fec_status fec_trace_enable(fec_ctx *ctx, int enable)
+{
+    if (!ctx) return FEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FEC_ERR_CUDA;
+    ctx->trace.acc.clear();
+    if (enable && !ctx->trace.init(512)) return FEC_ERR_CUDA;
+    ctx->tracing = enable != 0;
+    return FEC_OK;
+}
+
+int fec_trace_read(const fec_ctx *ctx, fec_trace_entry *out, int cap)
+{
+    if (!ctx || cap < 0) return -1;
+    const auto &acc = ctx->trace.acc;
+    if (out)
+        for (int i = 0; i < cap && i < (int)acc.size(); ++i) {
+            out[i].name = acc[i].name;
+            out[i].launches = acc[i].launches;
+            out[i].total_ms = acc[i].ms;
+        }
+    return (int)acc.size();
+}
+
+fec_status fec_get_stats(const fec_ctx *ctx, fec_stats *out)
+{
+    if (!ctx || !out) return FEC_ERR_INVALID_ARG;
+    *out = ctx->last;
+    return FEC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// fec_grid.cu -- voxel-grid construction: quantisation and bounding box,
+// grid keys, and the cell table built from the sorted keys.
+//
+// The grid replaces Algorithm 1's kd-tree (Section 2.2) and its radius query
+// FindNeighbor: with R = floor(sqrt(T2)) the largest per-axis offset of two
+// joined points, cells of side S = 2h >= R (h = ceil(R/2)) guarantee that every
+// joined pair lies in the same or an adjacent cell (27-cell stencil).  Each
+// cell is split into 2x2x2 sub-cells of side h; since 3(h-1)^2 <= T2, all
+// points of one sub-cell are pairwise within d, so a sub-cell is a clique and
+// becomes one union-find node.
+#include "fec_internal.cuh"
+
+namespace fec {
+
+namespace {
+
+__device__ __forceinline__ uint32_t bitlen(uint32_t v) { return v ? 32u - __clz(v) : 0u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace
+
+// Reset the plan for a call of n points.
+__global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
+{
+    const int t = threadIdx.x;
+    if (t < 3) {
+        plan->lo[t] = INT32_MAX;
+        plan->hi[t] = INT32_MIN;
+        plan->perm[t] = t;
+        plan->bits[t] = 0;
+    }
+    if (t == 0) {
+        plan->key_bits = 0;
+        plan->status = 0;
+        plan->M_s = 0;
+        plan->M_c = 0;
+        plan->n_big = 0;
+        plan->scan_tile_counter = 0;
+        plan->sort.n = n;
+        plan->sort.npasses = 0;
+        plan->sort.key64 = 0;
+        plan->kept.n = 0;
+        plan->kept.npasses = kept_passes;
+        plan->kept.key64 = 0;
+    }
+    for (int i = t; i < kMaxPasses * kRadixBins; i += blockDim.x) {
+        (&plan->sort.hist[0][0])[i] = 0;
+        (&plan->kept.hist[0][0])[i] = 0;
+    }
+    if (t < kMaxPasses) {
+        plan->sort.tile_counter[t] = 0;
+        plan->kept.tile_counter[t] = 0;
+    }
+}
+
+// a1: validate and quantise every coordinate, reduce the bounding box of q.
+__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, uint32_t n, Plan *plan)
+{
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    uint32_t st = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int32_t q;
+            const int e = quantize1(xyz[3 * (size_t)i + a], q);
+            if (e == 1) st |= ST_NONFINITE;
+            else if (e == 2) st |= ST_OUT_OF_RANGE;
+            else {
+                lo[a] = min(lo[a], q);
+                hi[a] = max(hi[a], q);
+            }
+        }
+    }
+    __shared__ int32_t s_lo[3][8], s_hi[3][8];
+    __shared__ uint32_t s_st;
+    if (threadIdx.x == 0) s_st = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int32_t vl = warp_min(lo[a]), vh = warp_max(hi[a]);
+        if (l == 0) {
+            s_lo[a][w] = vl;
+            s_hi[a][w] = vh;
+        }
+    }
+    if (st) atomicOr(&s_st, st);
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        int32_t vl = INT32_MAX, vh = INT32_MIN;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            vl = min(vl, s_lo[a][k]);
+            vh = max(vh, s_hi[a][k]);
+        }
+        if (vl != INT32_MAX) {
+            atomicMin(&plan->lo[a], vl);
+            atomicMax(&plan->hi[a], vh);
+        }
+    }
+    if (threadIdx.x == 0 && s_st) atomicOr(&plan->status, s_st);
+}
+
+// a1: choose the axis order (largest cell extent major, smallest minor) and
+// the key layout; disable the rest of the pipeline on a data error.
+__global__ void k_plan(Plan *plan, Params prm)
+{
+    if (threadIdx.x != 0) return;
+    if (plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) {
+        plan->sort.n = 0;
+        return;
+    }
+    uint32_t cm[3];
+    for (int a = 0; a < 3; ++a) {
+        const int64_t ext = (int64_t)plan->hi[a] - plan->lo[a];
+        cm[a] = (uint32_t)(ext / prm.S);
+    }
+    int perm[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (cm[perm[j]] > cm[perm[i]]) {
+                int t = perm[i];
+                perm[i] = perm[j];
+                perm[j] = t;
+            }
+    uint32_t total = 0;
+    for (int p = 0; p < 3; ++p) {
+        plan->perm[p] = perm[p];
+        plan->bits[p] = bitlen(cm[perm[p]]);
+        total += plan->bits[p];
+    }
+    if (total > 61) {
+        plan->status |= ST_KEY_OVERFLOW;
+        plan->sort.n = 0;
+        return;
+    }
+    if (cm[perm[0]] + 1 > prm.slab_cap) {  // cannot happen for |q| < 2^23
+        plan->status |= ST_SIZE_OVERFLOW;
+        plan->sort.n = 0;
+        return;
+    }
+    plan->key_bits = total + 3;
+    plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
+    plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
+}
+
+// Grid coordinates of a quantised point under the plan.
+struct GridMap {
+    int32_t lo[3];
+    int perm[3];
+    uint32_t bits[3];
+    int32_t S, h;
+
+    __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
+    {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = plan->lo[a];
+            perm[a] = plan->perm[a];
+            bits[a] = plan->bits[a];
+        }
+        S = prm.S;
+        h = prm.h;
+    }
+    // Sort key: [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2], c = cell coordinate,
+    // s = which half of the cell (sub-cell bit).
+    __device__ __forceinline__ unsigned long long key(const int32_t q[3]) const
+    {
+        unsigned long long k = 0;
+        uint32_t sub = 0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const uint32_t rel = (uint32_t)(q[perm[p]] - lo[perm[p]]);
+            const uint32_t c = rel / (uint32_t)S;
+            const uint32_t s = (rel - c * (uint32_t)S) >= (uint32_t)h ? 1u : 0u;
+            k = (k << bits[p]) | c;
+            sub = (sub << 1) | s;
+        }
+        return (k << 3) | sub;
+    }
+};
+
+// a1: grid keys of all points, plus the digit histograms of every radix pass.
+template <typename KeyT>
+__global__ void __launch_bounds__(256)
+    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, KeyT *__restrict__ keys)
+{
+    constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
+    SortCtl *ctl = &plan->sort;
+    if (ctl->key64 != want64) return;
+    const uint32_t n = ctl->n;
+    if (n == 0) return;
+    const int np = (int)ctl->npasses;
+    __shared__ uint32_t h[kMaxPasses][kRadixBins];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
+    GridMap g;
+    g.load(plan, prm);
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) quantize1(xyz[3 * (size_t)i + a], q[a]);
+        const KeyT k = (KeyT)g.key(q);
+        keys[i] = k;
+        for (int p = 0; p < np; ++p) atomicAdd(&h[p][(uint32_t)(k >> (p * kRadixBits)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&ctl->hist[i / kRadixBins][i % kRadixBins], v);
+    }
+}
+
+// a3: cell table from the sorted keys, in one pass with a decoupled look-back
+// scan of two head flags (new sub-cell, new cell).  Also gathers the sorted
+// point records (quantised coordinates + original index).
+//   sc_of[p]      sub-cell of sorted position p
+//   sc_start[a]   first sorted position of sub-cell a (sc_start[M_s] = n)
+//   cell_key[c]   cell key of cell c; cell_sc[c] first sub-cell of cell c
+template <typename KeyT>
+__global__ void __launch_bounds__(kScanThreads)
+    k_cells(Plan *plan, const KeyT *__restrict__ keys_a, const uint32_t *__restrict__ vals_a,
+            const KeyT *__restrict__ keys_b, const uint32_t *__restrict__ vals_b,
+            const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
+            uint32_t *__restrict__ sc_start, unsigned long long *__restrict__ cell_key,
+            uint32_t *__restrict__ cell_sc, unsigned long long *__restrict__ tstat)
+{
+    constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
+    const SortCtl *ctl = &plan->sort;
+    if (ctl->key64 != want64) return;
+    const uint32_t n = ctl->n;
+    if (n == 0) return;
+    const bool in_b = (ctl->npasses & 1u) != 0;
+    const KeyT *__restrict__ keys = in_b ? keys_b : keys_a;
+    const uint32_t *__restrict__ vals = in_b ? vals_b : vals_a;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+
+    constexpr unsigned long long kAgg = 1ull << 62, kIncl = 2ull << 62;
+    constexpr unsigned long long kMask = (1ull << 62) - 1;
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&plan->scan_tile_counter, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t p0 = tile * kScanTile + tid * kScanIPT;
+
+        KeyT k[kScanIPT];
+        unsigned long long flag[kScanIPT];  // (cell head << 31) | sub-cell head
+        KeyT prev = (p0 > 0 && p0 - 1 < n) ? keys[p0 - 1] : KeyT(0);
+        unsigned long long run = 0;
+#pragma unroll
+        for (int i = 0; i < kScanIPT; ++i) {
+            const uint32_t p = p0 + i;
+            unsigned long long f = 0;
+            if (p < n) {
+                k[i] = keys[p];
+                const bool sh = (p == 0) || k[i] != prev;
+                const bool ch = (p == 0) || (k[i] >> 3) != (prev >> 3);
+                f = ((unsigned long long)ch << 31) | (unsigned long long)sh;
+                prev = k[i];
+            } else {
+                k[i] = KeyT(0);
+            }
+            run += f;
+            flag[i] = run;  // inclusive within the thread
+        }
+        // block exclusive scan of the thread totals
+        unsigned long long incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < kScanThreads / 32; ++w) {
+                const unsigned long long v = s_warp[w];
+                s_warp[w] = tot;
+                tot += v;
+            }
+            // look-back over preceding tiles
+            unsigned long long prefix = 0;
+            if (tile == 0) {
+                st_relaxed64(tstat, kIncl | tot);
+            } else {
+                st_relaxed64(tstat + tile, kAgg | tot);
+                int64_t p = (int64_t)tile - 1;
+                uint32_t it = 0;
+                while (p >= 0) {
+                    const unsigned long long s = ld_relaxed64(tstat + p);
+                    const unsigned long long f = s & ~kMask;
+                    if (f == 0) {
+                        if (++it > kWaitCap) {
+                            atomicOr(&plan->status, ST_WAIT_TIMEOUT);
+                            break;
+                        }
+                        spin_pause(it);
+                        continue;
+                    }
+                    prefix += s & kMask;
+                    if (f == kIncl) break;
+                    --p;
+                }
+                st_relaxed64(tstat + tile, kIncl | ((prefix + tot) & kMask));
+            }
+            s_prefix = prefix;
+        }
+        __syncthreads();
+        const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
+
+        uint32_t vv[kScanIPT];
+#pragma unroll
+        for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : 0u;
+        unsigned long long before = base;
+#pragma unroll
+        for (int i = 0; i < kScanIPT; ++i) {
+            const uint32_t p = p0 + i;
+            if (p >= n) break;
+            const unsigned long long cur = base + flag[i];
+            const uint32_t sc = (uint32_t)(cur & 0x7fffffffull) - 1u;
+            const uint32_t c = (uint32_t)(cur >> 31) - 1u;
+            const bool sh = (cur & 0x7fffffffull) != (before & 0x7fffffffull);
+            const bool ch = (cur >> 31) != (before >> 31);
+            before = cur;
+            const uint32_t idx = vv[i];
+            if (sc >= n || c >= n || idx >= n) {  // only after a look-back timeout
+                atomicOr(&plan->status, ST_SIZE_OVERFLOW);
+                continue;
+            }
+            sc_of[p] = sc;
+            if (sh) sc_start[sc] = p;
+            if (ch) {
+                cell_key[c] = (unsigned long long)(k[i] >> 3);
+                cell_sc[c] = sc;
+            }
+            Rec r;
+            quantize1(xyz[3 * (size_t)idx + 0], r.x);
+            quantize1(xyz[3 * (size_t)idx + 1], r.y);
+            quantize1(xyz[3 * (size_t)idx + 2], r.z);
+            r.idx = idx;
+            rec[p] = r;
+            if (p == n - 1) {
+                plan->M_s = sc + 1;
+                plan->M_c = c + 1;
+                sc_start[sc + 1] = n;
+                cell_sc[c + 1] = sc + 1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// a3: per sub-cell box, count and smallest original index; initialise the
+// union-find and component arrays.  Sub-cells above kBigSubcell points are
+// queued for k_subcell_big.
+__global__ void __launch_bounds__(256)
+    k_subcell_stats(Plan *plan, const Rec *__restrict__ rec, const uint32_t *__restrict__ sc_start,
+                    SubBox *__restrict__ box, uint32_t *__restrict__ sminidx,
+                    uint32_t *__restrict__ parent, uint32_t *__restrict__ csize,
+                    uint32_t *__restrict__ cmin, int32_t *__restrict__ crank,
+                    uint32_t *__restrict__ big)
+{
+    const uint32_t M = plan->M_s;
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
+        parent[a] = a;
+        csize[a] = 0;
+        cmin[a] = 0xffffffffu;
+        crank[a] = -1;
+        const uint32_t s = sc_start[a], e = sc_start[a + 1];
+        if (s >= e || e > plan->sort.n) {  // only after a look-back timeout
+            atomicOr(&plan->status, ST_SIZE_OVERFLOW);
+            box[a] = SubBox{0, 0, 0, 0, 0, 0, 0, 0};
+            sminidx[a] = 0;
+            continue;
+        }
+        if (e - s > (uint32_t)kBigSubcell) {
+            big[atomicAdd(&plan->n_big, 1u)] = a;
+            continue;
+        }
+        SubBox b;
+        b.lx = b.ly = b.lz = INT32_MAX;
+        b.hx = b.hy = b.hz = INT32_MIN;
+        uint32_t mi = 0xffffffffu;
+        for (uint32_t p = s; p < e; ++p) {
+            const Rec r = rec[p];
+            b.lx = min(b.lx, r.x); b.hx = max(b.hx, r.x);
+            b.ly = min(b.ly, r.y); b.hy = max(b.hy, r.y);
+            b.lz = min(b.lz, r.z); b.hz = max(b.hz, r.z);
+            mi = min(mi, r.idx);
+        }
+        b.start = s;
+        b.count = e - s;
+        box[a] = b;
+        sminidx[a] = mi;
+    }
+}
+
+// a3: the same for the queued large sub-cells, one block per sub-cell.
+__global__ void __launch_bounds__(256)
+    k_subcell_big(Plan *plan, const Rec *__restrict__ rec, const uint32_t *__restrict__ sc_start,
+                  const uint32_t *__restrict__ big, SubBox *__restrict__ box,
+                  uint32_t *__restrict__ sminidx)
+{
+    __shared__ int32_t s_v[7][8];
+    const uint32_t nb = plan->n_big;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
+        const uint32_t a = big[j];
+        const uint32_t s = sc_start[a], e = sc_start[a + 1];
+        int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+        uint32_t mi = 0xffffffffu;
+        for (uint32_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+            const Rec r = rec[p];
+            lo[0] = min(lo[0], r.x); hi[0] = max(hi[0], r.x);
+            lo[1] = min(lo[1], r.y); hi[1] = max(hi[1], r.y);
+            lo[2] = min(lo[2], r.z); hi[2] = max(hi[2], r.z);
+            mi = min(mi, r.idx);
+        }
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+            lo[a3] = warp_min(lo[a3]);
+            hi[a3] = warp_max(hi[a3]);
+        }
+        mi = warp_min(mi);
+        if (l == 0) {
+            for (int a3 = 0; a3 < 3; ++a3) {
+                s_v[a3][w] = lo[a3];
+                s_v[3 + a3][w] = hi[a3];
+            }
+            s_v[6][w] = (int32_t)mi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            SubBox b;
+            int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+            uint32_t m = 0xffffffffu;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    L[a3] = min(L[a3], s_v[a3][k]);
+                    H[a3] = max(H[a3], s_v[3 + a3][k]);
+                }
+                m = min(m, (uint32_t)s_v[6][k]);
+            }
+            b.lx = L[0]; b.ly = L[1]; b.lz = L[2];
+            b.hx = H[0]; b.hy = H[1]; b.hz = H[2];
+            b.start = s;
+            b.count = e - s;
+            box[a] = b;
+            sminidx[a] = m;
+        }
+        __syncthreads();
+    }
+}
+
+// a3: slab index over the major cell coordinate: cells of slab x occupy
+// [slab_lo[x], slab_hi[x]) of the sorted cell array (empty: lo == hi == 0).
+__global__ void __launch_bounds__(256)
+    k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
+            uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi)
+{
+    const uint32_t M = plan->M_c;
+    const uint32_t sh = plan->bits[1] + plan->bits[2];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        const unsigned long long x = cell_key[c] >> sh;
+        if (c == 0 || (cell_key[c - 1] >> sh) != x) slab_lo[x] = c;
+        if (c + 1 == M || (cell_key[c + 1] >> sh) != x) slab_hi[x] = c + 1;
+    }
+}
+
+cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
+{
+    const int grid = ws.sms * 8;
+    k_init<<<1, 256, 0, st>>>(ws.plan, prm.n, (uint32_t)kept_sort_passes(prm.n));
+    FEC_MARK(ws, "k_init", st);
+    k_bbox<<<grid, 256, 0, st>>>(xyz, prm.n, ws.plan);
+    FEC_MARK(ws, "k_bbox", st);
+    k_plan<<<1, 32, 0, st>>>(ws.plan, prm);
+    FEC_MARK(ws, "k_plan", st);
+    k_keys<uint32_t><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a);
+    FEC_MARK(ws, "k_keys_u32", st);
+    k_keys<unsigned long long><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (unsigned long long *)ws.keys_a);
+    FEC_MARK(ws, "k_keys_u64", st);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
+{
+    const size_t ntiles = ((size_t)prm.n + kScanTile - 1) / kScanTile;
+    cudaError_t e = cudaMemsetAsync(ws.scan_status, 0, (ntiles + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    FEC_MARK(ws, "memset_scan_status", st);
+    const int grid = ws.sms * 8;
+    k_cells<uint32_t><<<grid, kScanThreads, 0, st>>>(
+        ws.plan, (const uint32_t *)ws.keys_a, ws.vals_a, (const uint32_t *)ws.keys_b, ws.vals_b, xyz,
+        ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc, ws.scan_status);
+    FEC_MARK(ws, "k_cells_u32", st);
+    k_cells<unsigned long long><<<grid, kScanThreads, 0, st>>>(
+        ws.plan, (const unsigned long long *)ws.keys_a, ws.vals_a,
+        (const unsigned long long *)ws.keys_b, ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start,
+        ws.cell_key, ws.cell_sc, ws.scan_status);
+    FEC_MARK(ws, "k_cells_u64", st);
+    k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.box, ws.sminidx,
+                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big);
+    FEC_MARK(ws, "k_subcell_stats", st);
+    k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.big, ws.box,
+                                              ws.sminidx);
+    FEC_MARK(ws, "k_subcell_big", st);
+    e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ws.slab_hi, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    FEC_MARK(ws, "memset_slabs", st);
+    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.slab_lo, ws.slab_hi);
+    FEC_MARK(ws, "k_slabs", st);
+    return cudaGetLastError();
+}
+
+}  // namespace fec

@@ -1,0 +1,296 @@
+// fec_internal.cuh -- device-side plan, workspace layout and helpers shared by
+// the CUDA translation units of the library (not part of the public ABI).
+//
+// The pipeline for one cloud (Eq. 1 as connected components; Algorithm 1's
+// input/output) runs without host round trips until the final read-back:
+//
+//   a1  quantise + bounding box + validation            k_bbox, k_plan
+//   a1  grid keys (cell of side S=2h, sub-cell bits)    k_keys (+ radix digit histograms)
+//   a2  LSD radix sort of (key, index), onesweep        k_onesweep (per 8-bit digit)
+//   a3  cell table: sub-cell/cell heads, scan, gather   k_cells, k_subcell_stats, k_slabs
+//   a4  neighbour test + union (27-cell stencil)        k_union
+//   a5  flatten + component statistics                  k_flatten_stats
+//   a6  size filter, order by smallest index, labels    k_kept, sort, k_rank, k_labels
+//
+// Sizes that only the device knows (key bits, cells, sub-cells, kept count)
+// live in Plan / SortCtl in device memory; kernels read them and grid-stride.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+namespace fec {
+
+// Status bits set by kernels (Plan::status).
+enum : uint32_t {
+    ST_NONFINITE = 1u << 0,
+    ST_OUT_OF_RANGE = 1u << 1,
+    ST_KEY_OVERFLOW = 1u << 2,     // cell key would need > 61 bits
+    ST_WAIT_TIMEOUT = 1u << 3,     // a look-back wait hit its cap
+    ST_UNION_CAP = 1u << 4,        // a union/find loop hit its cap
+    ST_SIZE_OVERFLOW = 1u << 5,    // a device count exceeded its buffer
+};
+
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;            // 64-bit keys
+constexpr int kSortThreads = 512;
+constexpr int kSortIPT = 8;              // items per thread
+constexpr int kSortTile = kSortThreads * kSortIPT;   // 4096 keys per tile
+constexpr int kScanThreads = 256;
+constexpr int kScanIPT = 8;
+constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
+constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a block
+constexpr uint32_t kWaitCap = 1u << 22;  // spin iterations before a wait gives up
+constexpr uint32_t kUnionCap = 1u << 20; // retries of one union before it gives up
+
+// Control block of one radix sort (device memory).
+struct SortCtl {
+    uint32_t n;         // number of keys
+    uint32_t npasses;   // 8-bit digit passes to run
+    uint32_t key64;     // 1: 64-bit keys, 0: 32-bit keys
+    uint32_t pad;
+    uint32_t hist[kMaxPasses][kRadixBins];   // digit counts of every pass
+    uint32_t tile_counter[kMaxPasses];       // dynamic tile ids of every pass
+};
+
+// Per-call plan (device memory), written by k_plan / k_cells / kernels.
+struct Plan {
+    int32_t lo[3], hi[3];      // bounding box of q per original axis
+    int32_t perm[3];           // permuted axis p -> original axis (p0 major .. p2 minor)
+    uint32_t bits[3];          // bits of the cell coordinate per permuted axis
+    uint32_t key_bits;         // total sort-key bits (cell key bits + 3)
+    uint32_t status;           // ST_* bits
+    uint32_t M_s, M_c;         // occupied sub-cells and cells
+    uint32_t n_big;            // sub-cells with more than kBigSubcell points
+    uint32_t scan_tile_counter;
+    uint32_t pad[2];
+    SortCtl sort;              // main (key, index) sort
+    SortCtl kept;              // sort of kept components by smallest index
+};
+
+// Host-side constants of one call, passed by value.
+struct Params {
+    uint32_t n;
+    int64_t T2;          // squared join radius in units^2
+    int32_t R;           // floor(sqrt(T2))
+    int32_t h;           // sub-cell side (units); cells have side S = 2h
+    int32_t S;
+    uint32_t slab_cap;   // entries of the slab index (>= max major cell coordinate + 1)
+};
+
+// Quantised point record in cell order: coordinates and the original index.
+struct __align__(16) Rec {
+    int32_t x, y, z;
+    uint32_t idx;
+};
+
+// Per sub-cell: bounding box, first record, record count, smallest index.
+struct __align__(16) SubBox {
+    int32_t lx, ly, lz;
+    uint32_t start;
+    int32_t hx, hy, hz;
+    uint32_t count;
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// q = rint(x * 1024) (round half to even).  x * 1024 is exact in float.
+// Returns 0 if valid, 1 if non-finite, 2 if |q| >= 2^23.
+__device__ __forceinline__ int quantize1(float x, int32_t &q)
+{
+    if (!isfinite(x)) {
+        q = 0;
+        return 1;
+    }
+    float r = rintf(x * 1024.0f);
+    if (fabsf(r) >= 8388608.0f) {
+        q = 0;
+        return 2;
+    }
+    q = __float2int_rn(r);
+    return 0;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Backoff inside bounded spin loops.
+__device__ __forceinline__ void spin_pause(uint32_t it)
+{
+    if (it > 16) __nanosleep(it > 1024 ? 256 : 32);
+}
+
+// Union-find over sub-cells.  Invariant: parent[x] <= x, roots satisfy
+// parent[r] == r, so the root of a set is its smallest member.
+__device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x)
+{
+    uint32_t cur = ld_relaxed(parent + x);
+    if (cur == x) return x;
+    uint32_t prev = x;
+    for (uint32_t it = 0; it < kUnionCap; ++it) {
+        uint32_t next = ld_relaxed(parent + cur);
+        if (next == cur) return cur;
+        // path halving: prev skips to cur's parent (still an ancestor)
+        st_relaxed(parent + prev, next);
+        prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+// Join the sets of a and b: hook the larger root under the smaller.
+// Returns false if the retry cap was hit (the caller flags ST_UNION_CAP).
+__device__ __forceinline__ bool uf_unite(uint32_t *parent, uint32_t a, uint32_t b)
+{
+    for (uint32_t it = 0; it < kUnionCap; ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return true;
+        if (a < b) {
+            uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        // a > b: make b the parent of root a, if a is still a root
+        uint32_t old = atomicCAS(parent + a, a, b);
+        if (old == a) return true;
+        a = old;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (one stream; all asynchronous)
+// ---------------------------------------------------------------------------
+
+// Device workspace of one context, carved from a single allocation.  All
+// arrays are sized for cap_n points (every per-cell / per-sub-cell array is
+// bounded by the number of points).
+struct Trace;  // per-launch CUDA-event tracing (fec_api.cu)
+
+struct Workspace {
+    Trace *trace = nullptr;        // non-null while tracing is enabled
+    int device = 0;
+    int sms = 0;
+    size_t cap_n = 0;
+    uint32_t slab_cap = 0;
+    void *base = nullptr;
+    size_t bytes = 0;
+    Plan *plan = nullptr;
+    float *xyz = nullptr;          // staging of host input
+    int32_t *labels = nullptr;     // staging of host output
+    void *keys_a = nullptr;        // 8 * cap_n bytes each (32- or 64-bit keys)
+    void *keys_b = nullptr;
+    uint32_t *vals_a = nullptr;
+    uint32_t *vals_b = nullptr;
+    uint32_t *sort_status = nullptr;
+    unsigned long long *scan_status = nullptr;
+    Rec *rec = nullptr;
+    uint32_t *sc_of = nullptr;
+    uint32_t *sc_start = nullptr;  // cap_n + 1
+    SubBox *box = nullptr;
+    uint32_t *sminidx = nullptr;
+    uint32_t *parent = nullptr;
+    uint32_t *csize = nullptr;
+    uint32_t *cmin = nullptr;
+    int32_t *crank = nullptr;
+    uint32_t *big = nullptr;
+    unsigned long long *cell_key = nullptr;
+    uint32_t *cell_sc = nullptr;   // cap_n + 1
+    uint32_t *slab_lo = nullptr;   // slab_cap
+    uint32_t *slab_hi = nullptr;
+    // The kept-component sort reuses the key buffers once the cell table is built.
+    uint32_t *kept_key_a() const { return (uint32_t *)keys_a; }
+    uint32_t *kept_val_a() const { return (uint32_t *)keys_a + cap_n; }
+    uint32_t *kept_key_b() const { return (uint32_t *)keys_b; }
+    uint32_t *kept_val_b() const { return (uint32_t *)keys_b + cap_n; }
+};
+
+// Record a trace mark named `name` after the launch just enqueued on st
+// (no-op unless tracing is enabled).
+void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
+#define FEC_MARK(ws, name, st) trace_mark((ws), (name), (st))
+
+// Bytes of a workspace for cap_n points and slab_cap slab entries; with a
+// non-null base, also carves the arrays into ws.
+size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap);
+
+// Host-side constants for n points at radius d.
+Params make_params(uint32_t n, float d);
+// Upper bound of 8-bit passes of the main sort over any cloud at this S.
+int max_sort_passes(const Params &prm);
+// Passes of the kept-component sort (keys are point indices < n).
+int kept_sort_passes(uint32_t n);
+
+// a1 (init, bbox, plan, keys) for n points at xyz (device).
+cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st);
+// a3 (cell table, sub-cell stats, slab index).
+cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st);
+// a4 + a5 + kept list of a6.
+cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
+                          long long max_size, cudaStream_t st);
+// a6 rank + labels (labels: device pointer, n entries).
+cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, cudaStream_t st);
+// The whole pipeline for one cloud (device pointers), no host synchronisation.
+cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
+                            long long min_size, long long max_size, int32_t *labels,
+                            cudaStream_t st);
+
+// Onesweep radix sort of (key, value) over ctl->npasses 8-bit digits, with
+// digit histograms already in ctl->hist.  Values may be null (identity index
+// 0..n-1 for the first pass).  Kernels for the key width that ctl->key64 does
+// not select return at once, so both widths can be enqueued blindly.
+// Result lands in keys_a/vals_a if npasses is even, else keys_b/vals_b.
+cudaError_t launch_sort_u32(const Workspace &ws, const char *name, SortCtl *ctl, uint32_t *keys_a,
+                            uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
+                            bool identity_vals, uint32_t *tile_status, uint32_t max_n,
+                            int max_passes, int grid, cudaStream_t st, uint32_t *status);
+cudaError_t launch_sort_u64(const Workspace &ws, const char *name, SortCtl *ctl,
+                            unsigned long long *keys_a, uint32_t *vals_a,
+                            unsigned long long *keys_b, uint32_t *vals_b, bool identity_vals,
+                            uint32_t *tile_status, uint32_t max_n, int max_passes, int grid,
+                            cudaStream_t st, uint32_t *status);
+// uint32 words of look-back status a sort of up to max_n keys needs.
+inline size_t sort_status_words(uint32_t max_n)
+{
+    return 2 * (((size_t)max_n + kSortTile - 1) / kSortTile + 1) * kRadixBins;
+}
+// Digit histograms of all passes for 32-bit keys already in memory.
+cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st);
+
+int sm_count();
+
+}  // namespace fec

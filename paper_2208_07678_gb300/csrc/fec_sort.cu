@@ -1,0 +1,275 @@
+// fec_sort.cu -- LSD radix sort of (key, uint32 value) pairs, one kernel per
+// 8-bit digit ("onesweep": every tile ranks its keys stably in shared memory,
+// finds its global digit offsets by decoupled look-back over the preceding
+// tiles, and writes each digit run coalesced).  Replaces the kd-tree build of
+// Algorithm 1 (Section 2.2): sorting by grid-cell key groups every cell's
+// points contiguously.
+//
+// Digit histograms of all passes are computed up front (fused into the key
+// kernel for the main sort), so a pass reads each key and value once and
+// writes them once.  Look-back waits are bounded (kWaitCap); a timeout sets
+// ST_WAIT_TIMEOUT and the pass continues with a wrong prefix instead of
+// hanging.  Tile ids are taken from an atomic counter, so a tile only ever
+// waits on tiles already owned by running blocks.
+#include "fec_internal.cuh"
+
+namespace fec {
+
+namespace {
+
+constexpr int kWarps = kSortThreads / 32;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagIncl = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+template <typename KeyT>
+struct SortSmem {
+    KeyT keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint16_t wcnt[kWarps][kRadixBins];
+    uint32_t gofs[kRadixBins];   // exclusive global offset of each digit (whole pass)
+    uint32_t cnt[kRadixBins];    // tile count of each digit
+    uint32_t excl[kRadixBins];   // tile-local exclusive offset of each digit
+    uint32_t base[kRadixBins];   // output index = base[d] + tile-local position
+    uint32_t warp_tot[kRadixBins / 32];
+    uint32_t tile;
+};
+
+// Exclusive scan of in[0..255] into out[], by the first 256 threads.
+__device__ __forceinline__ void scan256(const uint32_t *in, uint32_t *out, uint32_t *warp_tot)
+{
+    const int t = threadIdx.x;
+    uint32_t v = 0, incl = 0;
+    if (t < kRadixBins) {
+        v = in[t];
+        incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((t & 31) >= o) incl += u;
+        }
+        if ((t & 31) == 31) warp_tot[t >> 5] = incl;
+    }
+    __syncthreads();
+    if (t < kRadixBins) {
+        uint32_t add = 0;
+        for (int w = 0; w < (t >> 5); ++w) add += warp_tot[w];
+        out[t] = add + incl - v;
+    }
+    __syncthreads();
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads)
+    k_onesweep(SortCtl *__restrict__ ctl, const KeyT *__restrict__ kin,
+               const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
+               uint32_t *__restrict__ vout, uint32_t *__restrict__ tstat_base, size_t tstride,
+               int pass, uint32_t *__restrict__ status)
+{
+    // Two look-back status arrays alternate between passes: this pass reads
+    // and publishes in `tstat`, and clears its own tiles' slots in the other
+    // array for the next pass (which starts only after this one finishes).
+    uint32_t *__restrict__ tstat = tstat_base + (size_t)(pass & 1) * tstride;
+    uint32_t *__restrict__ tnext = tstat_base + (size_t)((pass + 1) & 1) * tstride;
+    constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
+    if (ctl->key64 != want64 || (uint32_t)pass >= ctl->npasses) return;
+    const uint32_t n = ctl->n;
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const int shift = pass * kRadixBits;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem<KeyT> &S = *reinterpret_cast<SortSmem<KeyT> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid < kRadixBins) S.cnt[tid] = ctl->hist[pass][tid];
+    __syncthreads();
+    scan256(S.cnt, S.gofs, S.warp_tot);
+
+    for (;;) {
+        if (tid == 0) S.tile = atomicAdd(&ctl->tile_counter[pass], 1u);
+        for (int i = tid; i < kWarps * kRadixBins; i += kSortThreads)
+            (&S.wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t tile = S.tile;
+        if (tile >= ntiles) break;
+
+        KeyT key[kSortIPT];
+        uint32_t val[kSortIPT], lrank[kSortIPT], dig[kSortIPT];
+        const uint32_t seg = tile * (uint32_t)kSortTile + warp * (32u * kSortIPT);
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t pos = seg + r * 32 + lane;
+            const bool valid = pos < n;
+            key[r] = valid ? kin[pos] : KeyT(0);
+            val[r] = valid ? (vin ? vin[pos] : pos) : 0u;
+            const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRadixBins - 1)
+                                     : (uint32_t)kRadixBins + lane;
+            dig[r] = d;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (valid && lane == leader) {
+                old = S.wcnt[warp][d];
+                S.wcnt[warp][d] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            lrank[r] = old + __popc(peers & lanemask_lt());
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // Per digit: exclusive offsets of each warp inside the tile.
+        if (tid < kRadixBins) {
+            tnext[(size_t)tile * kRadixBins + tid] = 0;
+            uint32_t run = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                uint32_t c = S.wcnt[w][tid];
+                S.wcnt[w][tid] = (uint16_t)run;
+                run += c;
+            }
+            S.cnt[tid] = run;
+            // publish this tile's digit count for later tiles
+            st_relaxed(tstat + (size_t)tile * kRadixBins + tid,
+                       (tile == 0 ? kFlagIncl : kFlagAgg) | run);
+        }
+        __syncthreads();
+        scan256(S.cnt, S.excl, S.warp_tot);
+
+        // Decoupled look-back: sum the digit counts of all preceding tiles.
+        if (tid < kRadixBins) {
+            uint32_t prefix = 0;
+            if (tile > 0) {
+                int64_t p = (int64_t)tile - 1;
+                uint32_t it = 0;
+                while (p >= 0) {
+                    const uint32_t s = ld_relaxed(tstat + (size_t)p * kRadixBins + tid);
+                    const uint32_t f = s & ~kValMask;
+                    if (f == 0) {
+                        if (++it > kWaitCap) {
+                            atomicOr(status, ST_WAIT_TIMEOUT);
+                            break;
+                        }
+                        spin_pause(it);
+                        continue;
+                    }
+                    prefix += s & kValMask;
+                    if (f == kFlagIncl) break;
+                    --p;
+                }
+                st_relaxed(tstat + (size_t)tile * kRadixBins + tid,
+                           kFlagIncl | ((prefix + S.cnt[tid]) & kValMask));
+            }
+            S.base[tid] = S.gofs[tid] + prefix - S.excl[tid];
+        }
+        __syncthreads();
+
+        // Stage in tile-sorted order, then write digit runs coalesced.
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t pos = seg + r * 32 + lane;
+            if (pos < n) {
+                const uint32_t d = dig[r];
+                const uint32_t lp = S.excl[d] + S.wcnt[warp][d] + lrank[r];
+                S.keys[lp] = key[r];
+                S.vals[lp] = val[r];
+            }
+        }
+        __syncthreads();
+        const uint32_t tile_n = min((uint32_t)kSortTile, n - tile * (uint32_t)kSortTile);
+        for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+            const KeyT k = S.keys[i];
+            const uint32_t d = (uint32_t)(k >> shift) & (kRadixBins - 1);
+            const uint32_t o = S.base[d] + i;
+            if (o < n) {  // only false after a look-back timeout
+                kout[o] = k;
+                vout[o] = S.vals[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Digit histograms of every pass for 32-bit keys (count read from ctl).
+__global__ void __launch_bounds__(256) k_hist_u32(SortCtl *__restrict__ ctl,
+                                                   const uint32_t *__restrict__ keys)
+{
+    __shared__ uint32_t h[4][kRadixBins];
+    const uint32_t n = ctl->n;
+    const int np = min((int)ctl->npasses, 4);
+    for (int i = threadIdx.x; i < 4 * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < np; ++p) atomicAdd(&h[p][(k >> (p * kRadixBits)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&ctl->hist[i / kRadixBins][i % kRadixBins], v);
+    }
+}
+
+template <typename KeyT>
+cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, KeyT *ka, uint32_t *va,
+                        KeyT *kb, uint32_t *vb,
+                        bool identity_vals, uint32_t *tile_status, uint32_t max_n,
+                        int max_passes, int grid, cudaStream_t st, uint32_t *status)
+{
+    const size_t smem = sizeof(SortSmem<KeyT>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const size_t tstride = sort_status_words(max_n) / 2;
+    cudaError_t e = cudaMemsetAsync(tile_status, 0, tstride * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    FEC_MARK(ws, "memset_sort_status", st);
+    KeyT *kin = ka, *kout = kb;
+    uint32_t *vin = va, *vout = vb;
+    for (int p = 0; p < max_passes; ++p) {
+        k_onesweep<KeyT><<<grid, kSortThreads, smem, st>>>(ctl, kin, (p == 0 && identity_vals) ? nullptr : vin,
+                                                          kout, vout, tile_status, tstride, p, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        FEC_MARK(ws, name, st);
+        KeyT *tk = kin;
+        kin = kout;
+        kout = tk;
+        uint32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_sort_u32(const Workspace &ws, const char *name, SortCtl *ctl, uint32_t *keys_a,
+                            uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
+                            bool identity_vals, uint32_t *tile_status, uint32_t max_n,
+                            int max_passes, int grid, cudaStream_t st, uint32_t *status)
+{
+    return launch_sort<uint32_t>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                 tile_status, max_n, max_passes, grid, st, status);
+}
+
+cudaError_t launch_sort_u64(const Workspace &ws, const char *name, SortCtl *ctl,
+                            unsigned long long *keys_a, uint32_t *vals_a,
+                            unsigned long long *keys_b, uint32_t *vals_b, bool identity_vals,
+                            uint32_t *tile_status, uint32_t max_n, int max_passes, int grid,
+                            cudaStream_t st, uint32_t *status)
+{
+    return launch_sort<unsigned long long>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                           tile_status, max_n, max_passes, grid, st, status);
+}
+
+cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st)
+{
+    k_hist_u32<<<grid, 256, 0, st>>>(ctl, keys);
+    return cudaGetLastError();
+}
+
+}  // namespace fec

@@ -1,0 +1,115 @@
+"""Batched and served clustering: every frame's / request's labels equal the
+one-cloud call on that cloud alone (exact, tolerance 0), and match the
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_07678_gb300 import fec, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2208_07678_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    c = fec.Context(device=0)
+    yield c
+    c.close()
+
+
+def small_batch(n_frames=12, seed=41):
+    frames = synth.batch_256(seed=seed, n_frames=n_frames, lo=2_000, hi=40_000)
+    offs = np.zeros(n_frames + 1, np.int64)
+    offs[1:] = np.cumsum([f.n for f in frames])
+    xyz = np.concatenate([f.xyz for f in frames])
+    return frames, offs, xyz
+
+
+@pytest.mark.parametrize("device", [True, False], ids=["device", "host"])
+def test_batch_equals_single_and_oracle(ctx, device):
+    import torch
+
+    frames, offs, xyz = small_batch()
+    d = [f.d for f in frames]
+    mn = [f.min_size for f in frames]
+    mx = [f.max_size for f in frames]
+    x = torch.from_numpy(xyz).cuda() if device else xyz
+    labels, ks = ctx.cluster_batch(x, offs, d, mn, mx)
+    if device:
+        labels = labels.cpu().numpy()
+    for f, fr in enumerate(frames):
+        got = labels[offs[f]:offs[f + 1]]
+        alone, k_alone = ctx.cluster(fr.xyz, fr.d, fr.min_size, fr.max_size)
+        want, kw = oracle.cluster(fr.xyz, fr.d, fr.min_size, fr.max_size)
+        assert ks[f] == k_alone == kw
+        np.testing.assert_array_equal(got, alone)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_batch_with_empty_frames(ctx):
+    frames, offs, xyz = small_batch(4, seed=43)
+    # insert empty frames at the start, middle and end
+    offs2 = np.array([0, 0, offs[1], offs[2], offs[2], offs[3], offs[4], offs[4]], np.int64)
+    src = [None, 0, 1, None, 2, 3, None]
+    d = [0.3 if s is None else frames[s].d for s in src]
+    labels, ks = ctx.cluster_batch(xyz, offs2, d, [50] * 7, [50_000] * 7)
+    for f, s in enumerate(src):
+        if s is None:
+            assert ks[f] == 0
+            continue
+        want, kw = oracle.cluster(frames[s].xyz, frames[s].d, 50, 50_000)
+        assert ks[f] == kw
+        np.testing.assert_array_equal(labels[offs2[f]:offs2[f + 1]], want)
+
+
+def test_batch_error_in_one_frame(ctx):
+    frames, offs, xyz = small_batch(3, seed=44)
+    bad = xyz.copy()
+    bad[offs[1] + 5, 0] = np.nan
+    with pytest.raises(fec.FecError) as e:
+        ctx.cluster_batch(bad, offs, [f.d for f in frames], [1] * 3, [fec.INT64_MAX] * 3)
+    assert e.value.name == "FEC_ERR_NONFINITE"
+
+
+def test_serve_results_equal_alone():
+    """Requests submitted together overlap on the device; each result is the
+    same as clustering that request alone."""
+    reqs = [synth.serve_request(5, i, lo=5_000, hi=400_000) for i in range(10)]
+    with fec.Context(device=0) as srv, fec.Context(device=0) as solo:
+        outs = [np.full(r.n, -7, np.int32) for r in reqs]
+        tickets = [srv.submit(r.xyz, r.d, r.min_size, r.max_size, o) for r, o in zip(reqs, outs)]
+        for r, o, t in zip(reqs, outs, tickets):
+            st, k = srv.poll(t, -1)
+            assert st == fec.FEC_OK
+            alone, k_alone = solo.cluster(r.xyz, r.d, r.min_size, r.max_size)
+            assert k == k_alone
+            np.testing.assert_array_equal(o, alone)
+        # oracle on two of them
+        for r, o in list(zip(reqs, outs))[:2]:
+            want, _ = oracle.cluster(r.xyz, r.d, r.min_size, r.max_size)
+            np.testing.assert_array_equal(o, want)
+
+
+def test_serve_poll_semantics():
+    with fec.Context(device=0) as srv:
+        r = synth.serve_request(5, 3, lo=50_000, hi=60_000)
+        out = np.zeros(r.n, np.int32)
+        t = srv.submit(r.xyz, r.d, r.min_size, r.max_size, out)
+        st, _ = srv.poll(t, -1)
+        assert st == fec.FEC_OK
+        st, _ = srv.poll(t, 0)  # released
+        assert fec.STATUS[st] == "FEC_ERR_INVALID_ARG"
+
+
+def test_serve_rejects_over_budget():
+    with fec.Context(device=0, mem_budget_bytes=1 << 20) as srv:
+        xyz = np.zeros((100_000, 3), np.float32)
+        with pytest.raises(fec.FecError) as e:
+            srv.submit(xyz, 0.3, 1, 10, np.zeros(100_000, np.int32))
+        assert e.value.name == "FEC_ERR_BUSY"
