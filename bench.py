@@ -43,13 +43,14 @@ KERNEL_BYTES = {
     "onesweep_u32": lambda n, Ms, Mc: 16 * n,
     "k_cells_u32": lambda n, Ms, Mc: 40 * n + 4 * Ms + 12 * Mc,
     "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 56 * Ms,
-    "k_union": lambda n, Ms, Mc: 12 * Mc + 40 * Ms,
+    "k_local": lambda n, Ms, Mc: 4 * Mc + 56 * Ms,
+    "k_global": lambda n, Ms, Mc: 12 * Mc + 44 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
     "k_labels": lambda n, Ms, Mc: 12 * n,
 }
 KERNEL_SOURCE = {
     "k_bbox": "fec_grid.cu", "k_keys_u32": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
-    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_union": "fec_union.cu",
+    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_local": "fec_union.cu", "k_global": "fec_union.cu",
     "k_flatten_stats": "fec_union.cu", "k_labels": "fec_union.cu",
 }
 HOUSEKEEPING = ("memset", "h2d", "d2h", "summary")
@@ -160,6 +161,8 @@ def make_workload(name):
         return synth.frame_120k()
     if name == "blobs_20k":
         return synth.blobs_20k()
+    if name.startswith("map_frames:"):  # a shorter corridor map (same density), for profiling
+        return synth.map_27m(n_frames=int(name.split(":")[1]))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -341,6 +344,9 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "union_work": {k: stats[k] for k in ("pair_checks", "pair_box_joins", "pair_point_tests",
+                                                 "pair_same_root", "point_evals",
+                                                 "pairs_queued")},
             "trace_ms_per_step": {"total": round(step_total_ms, 4), "traced_step_ms": ms_traced,
                                   "by_kernel": breakdown},
         }

@@ -76,6 +76,12 @@ typedef struct {
     int32_t R;                /* floor(sqrt(T2)): largest joined offset per axis, units */
     int32_t h;                /* sub-cell side, units */
     int64_t T2;               /* squared join radius, units^2 */
+    int64_t pair_checks;      /* sub-cell pairs examined by the neighbour step */
+    int64_t pair_box_joins;   /* ... joined from their bounding boxes alone */
+    int64_t pair_point_tests; /* ... that needed point-level tests */
+    int64_t pair_same_root;   /* ... of those, skipped as already joined */
+    int64_t point_evals;      /* point-level distance evaluations */
+    int64_t pairs_queued;     /* pairs deferred to the warp-per-pair pass */
 } fec_stats;
 
 /* Create a context on options->device (options may be NULL: device 0, no

@@ -103,6 +103,10 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.cell_sc = (uint32_t *)take(4 * (n + 2));
     ws.slab_lo = (uint32_t *)take(4 * (size_t)slab_cap);
     ws.slab_hi = (uint32_t *)take(4 * (size_t)slab_cap);
+    ws.pairq_cap = n;
+    ws.pairq = (uint2 *)take(sizeof(uint2) * n);
+    ws.reps = (Rec *)take(sizeof(Rec) * n);
+    ws.lroot = (uint32_t *)take(4 * n);
     off = (off + 255) & ~(size_t)255;
     if (base) {
         ws.base = base;
@@ -159,6 +163,7 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
 // Small summary of a finished call, packed on the device for one copy.
 struct Summary {
     uint32_t status, k, M_s, M_c, key_bits, pad[3];
+    unsigned long long ctr[8];
 };
 
 __global__ void k_summary(const Plan *plan, Summary *out)
@@ -170,6 +175,7 @@ __global__ void k_summary(const Plan *plan, Summary *out)
         out->M_c = plan->M_c;
         out->key_bits = plan->key_bits;
     }
+    if (threadIdx.x < 8) out->ctr[threadIdx.x] = plan->ctr[threadIdx.x];
 }
 
 fec_status status_from_bits(uint32_t s)
@@ -343,6 +349,12 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
     st.R = prm.R;
     st.h = prm.h;
     st.T2 = prm.T2;
+    st.pair_checks = (int64_t)s.ctr[CTR_PAIRS];
+    st.pair_box_joins = (int64_t)s.ctr[CTR_BOX_JOINS];
+    st.pair_point_tests = (int64_t)s.ctr[CTR_POINT_TESTS];
+    st.pair_same_root = (int64_t)s.ctr[CTR_SAME_ROOT];
+    st.point_evals = (int64_t)s.ctr[CTR_POINT_EVALS];
+    st.pairs_queued = (int64_t)s.ctr[CTR_QUEUED];
     const fec_status f = status_from_bits(s.status);
     if (f == FEC_OK && num_clusters) *num_clusters = (int32_t)s.k;
     return f;

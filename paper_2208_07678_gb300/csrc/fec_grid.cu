@@ -50,6 +50,9 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->M_c = 0;
         plan->n_big = 0;
         plan->scan_tile_counter = 0;
+        plan->union_counter = 0;
+        plan->pairq_n = 0;
+        plan->local_counter = 0;
         plan->sort.n = n;
         plan->sort.npasses = 0;
         plan->sort.key64 = 0;
@@ -61,6 +64,7 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         (&plan->sort.hist[0][0])[i] = 0;
         (&plan->kept.hist[0][0])[i] = 0;
     }
+    if (t < 8) plan->ctr[t] = 0;
     if (t < kMaxPasses) {
         plan->sort.tile_counter[t] = 0;
         plan->kept.tile_counter[t] = 0;
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(256)
                     SubBox *__restrict__ box, uint32_t *__restrict__ sminidx,
                     uint32_t *__restrict__ parent, uint32_t *__restrict__ csize,
                     uint32_t *__restrict__ cmin, int32_t *__restrict__ crank,
-                    uint32_t *__restrict__ big)
+                    uint32_t *__restrict__ big, Rec *__restrict__ reps)
 {
     const uint32_t M = plan->M_s;
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
@@ -392,6 +396,7 @@ __global__ void __launch_bounds__(256)
             atomicOr(&plan->status, ST_SIZE_OVERFLOW);
             box[a] = SubBox{0, 0, 0, 0, 0, 0, 0, 0};
             sminidx[a] = 0;
+            reps[a] = Rec{0, 0, 0, 0};
             continue;
         }
         if (e - s > (uint32_t)kBigSubcell) {
@@ -413,6 +418,20 @@ __global__ void __launch_bounds__(256)
         b.count = e - s;
         box[a] = b;
         sminidx[a] = mi;
+        // representative: the point nearest the box centre (doubled units)
+        const int cx = b.lx + b.hx, cy = b.ly + b.hy, cz = b.lz + b.hz;
+        float best = __int_as_float(0x7f800000);
+        Rec rp = rec[s];
+        for (uint32_t p = s; p < e; ++p) {
+            const Rec r = rec[p];
+            const float dx = (float)(2 * r.x - cx), dy = (float)(2 * r.y - cy), dz = (float)(2 * r.z - cz);
+            const float dd = dx * dx + dy * dy + dz * dz;
+            if (dd < best) {
+                best = dd;
+                rp = r;
+            }
+        }
+        reps[a] = rp;
     }
 }
 
@@ -420,9 +439,11 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_subcell_big(Plan *plan, const Rec *__restrict__ rec, const uint32_t *__restrict__ sc_start,
                   const uint32_t *__restrict__ big, SubBox *__restrict__ box,
-                  uint32_t *__restrict__ sminidx)
+                  uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
 {
     __shared__ int32_t s_v[7][8];
+    __shared__ unsigned long long s_k[8];
+    __shared__ SubBox s_box;
     const uint32_t nb = plan->n_big;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
@@ -468,6 +489,31 @@ __global__ void __launch_bounds__(256)
             b.count = e - s;
             box[a] = b;
             sminidx[a] = m;
+            s_box = b;
+        }
+        __syncthreads();
+        // representative: the point nearest the box centre
+        const SubBox b = s_box;
+        const int cx = b.lx + b.hx, cy = b.ly + b.hy, cz = b.lz + b.hz;
+        unsigned long long bk = ~0ull;
+        for (uint32_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+            const Rec r = rec[p];
+            const float dx = (float)(2 * r.x - cx), dy = (float)(2 * r.y - cy), dz = (float)(2 * r.z - cz);
+            const unsigned long long k =
+                ((unsigned long long)__float_as_uint(dx * dx + dy * dy + dz * dz) << 32) | (p - s);
+            bk = k < bk ? k : bk;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, bk, o);
+            bk = u < bk ? u : bk;
+        }
+        if (l == 0) s_k[w] = bk;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = s_k[0];
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = s_k[k] < m ? s_k[k] : m;
+            reps[a] = rec[s + (uint32_t)m];
         }
         __syncthreads();
     }
@@ -521,10 +567,10 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
         ws.cell_key, ws.cell_sc, ws.scan_status);
     FEC_MARK(ws, "k_cells_u64", st);
     k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.box, ws.sminidx,
-                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big);
+                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);
     FEC_MARK(ws, "k_subcell_stats", st);
     k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.big, ws.box,
-                                              ws.sminidx);
+                                              ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_big", st);
     e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;

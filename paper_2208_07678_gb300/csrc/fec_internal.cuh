@@ -34,6 +34,16 @@ enum : uint32_t {
     ST_SIZE_OVERFLOW = 1u << 5,    // a device count exceeded its buffer
 };
 
+// Work counters of the union step (Plan::ctr).
+enum {
+    CTR_PAIRS = 0,        // sub-cell pairs examined
+    CTR_BOX_JOINS = 1,    // pairs joined by the box-diameter test alone
+    CTR_POINT_TESTS = 2,  // pairs that needed point-level tests
+    CTR_SAME_ROOT = 3,    // ... of which skipped because already joined
+    CTR_POINT_EVALS = 4,  // point-level distance evaluations
+    CTR_QUEUED = 5,       // pairs queued for the warp-per-pair kernel
+};
+
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;            // 64-bit keys
@@ -67,7 +77,11 @@ struct Plan {
     uint32_t M_s, M_c;         // occupied sub-cells and cells
     uint32_t n_big;            // sub-cells with more than kBigSubcell points
     uint32_t scan_tile_counter;
-    uint32_t pad[2];
+    uint32_t union_counter;     // dynamic cell chunks of the union step
+    uint32_t pairq_n;           // pairs queued for point-level tests
+    uint32_t local_counter;     // dynamic cell chunks of the in-cell step
+    uint32_t pad2[3];
+    unsigned long long ctr[8];  // work counters of the union step (CTR_*)
     SortCtl sort;              // main (key, index) sort
     SortCtl kept;              // sort of kept components by smallest index
 };
@@ -232,6 +246,10 @@ struct Workspace {
     uint32_t *cell_sc = nullptr;   // cap_n + 1
     uint32_t *slab_lo = nullptr;   // slab_cap
     uint32_t *slab_hi = nullptr;
+    uint2 *pairq = nullptr;        // sub-cell pairs queued for point tests
+    Rec *reps = nullptr;           // per sub-cell: its point nearest the box centre
+    uint32_t *lroot = nullptr;     // per sub-cell: smallest sub-cell of its in-cell component
+    size_t pairq_cap = 0;
     // The kept-component sort reuses the key buffers once the cell table is built.
     uint32_t *kept_key_a() const { return (uint32_t *)keys_a; }
     uint32_t *kept_val_a() const { return (uint32_t *)keys_a + cap_n; }

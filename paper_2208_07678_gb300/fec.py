@@ -48,7 +48,10 @@ class fec_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("cells", ctypes.c_int64), ("subcells", ctypes.c_int64),
                 ("num_clusters", ctypes.c_int64), ("key_bits", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("R", ctypes.c_int32), ("h", ctypes.c_int32),
-                ("T2", ctypes.c_int64)]
+                ("T2", ctypes.c_int64), ("pair_checks", ctypes.c_int64),
+                ("pair_box_joins", ctypes.c_int64), ("pair_point_tests", ctypes.c_int64),
+                ("pair_same_root", ctypes.c_int64), ("point_evals", ctypes.c_int64),
+                ("pairs_queued", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
