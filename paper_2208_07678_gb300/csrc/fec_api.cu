@@ -103,10 +103,22 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.cell_sc = (uint32_t *)take(4 * (n + 2));
     ws.slab_lo = (uint32_t *)take(4 * (size_t)slab_cap);
     ws.slab_hi = (uint32_t *)take(4 * (size_t)slab_cap);
-    ws.pairq_cap = n;
-    ws.pairq = (uint2 *)take(sizeof(uint2) * n);
+    const size_t lists = 2 * n * (size_t)(ws.list_scale ? ws.list_scale : 1);
+    ws.pairq_cap = lists;
+    ws.pairq = (uint2 *)take(sizeof(uint2) * lists);
     ws.reps = (Rec *)take(sizeof(Rec) * n);
-    ws.lroot = (uint32_t *)take(4 * n);
+    // dense column index: 2^col_bits entries, about 4 per point (64 Ki..64 Mi)
+    uint32_t cb = 16;
+    while (cb < 26 && ((size_t)1 << cb) < 4 * n) ++cb;
+    ws.col_bits = cb;
+    ws.col_lo = (uint32_t *)take(4 * ((size_t)1 << cb));
+    ws.col_hi = (uint32_t *)take(4 * ((size_t)1 << cb));
+    ws.edges_cap = lists;
+    ws.edges = (uint2 *)take(sizeof(uint2) * lists);
+    ws.nb_first = (uint32_t *)take(4 * 13 * n);
+    ws.nb_cnt = (uint8_t *)take(16 * n);
+    ws.scratch_words = (size_t)region_grid(ws, n) * kRegionScratch;
+    ws.scratch = (uint32_t *)take(4 * ws.scratch_words);
     off = (off + 255) & ~(size_t)255;
     if (base) {
         ws.base = base;
@@ -125,7 +137,8 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
                             long long min_size, long long max_size, int32_t *labels,
                             cudaStream_t st)
 {
-    const Params prm = make_params(n, d);
+    Params prm = make_params(n, d);
+    prm.col_bits = ws.col_bits;
     const int sort_grid = ws.sms * 2;
     cudaError_t e = enqueue_front(ws, xyz, prm, st);
     if (e != cudaSuccess) return e;
@@ -184,6 +197,7 @@ fec_status status_from_bits(uint32_t s)
     if (s & (ST_OUT_OF_RANGE | ST_KEY_OVERFLOW)) return FEC_ERR_OUT_OF_RANGE;
     if (s & (ST_WAIT_TIMEOUT | ST_UNION_CAP)) return FEC_ERR_NOT_CONVERGED;
     if (s & ST_SIZE_OVERFLOW) return FEC_ERR_OUT_OF_RANGE;
+    if (s & ST_QUEUE_OVERFLOW) return FEC_ERR_OOM;
     return FEC_OK;
 }
 
@@ -305,15 +319,17 @@ fec_status check_args(int64_t n, float d, int64_t min_size, int64_t max_size)
 }
 
 // Grow the workspace to hold n points at slab capacity slab_cap.
-fec_status ensure_workspace(fec_ctx *ctx, size_t n, uint32_t slab_cap)
+fec_status ensure_workspace(fec_ctx *ctx, size_t n, uint32_t slab_cap, bool force = false)
 {
     Workspace &ws = ctx->ws;
-    if (ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
+    if (!force && ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
     size_t cap = n;
     if (ws.base && cap < ws.cap_n + ws.cap_n / 4) cap = ws.cap_n + ws.cap_n / 4;
     if (cap < 4096) cap = 4096;
     uint32_t sc = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
     Workspace probe;
+    probe.sms = ws.sms;
+    probe.list_scale = ws.list_scale;
     size_t bytes = workspace_layout(probe, nullptr, cap, sc);
     if (ctx->budget && bytes > ctx->budget) {
         cap = n;  // retry without headroom
@@ -364,6 +380,10 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
 
 namespace fec {
 
+fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                        int64_t max_size, int32_t *labels, int32_t *num_clusters,
+                        const Params &prm);
+
 // One cloud on the context's stream; device or host pointers.  Caller holds ctx->mu.
 fec_status cluster_locked(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
                           int64_t max_size, int32_t *labels, int32_t *num_clusters)
@@ -371,6 +391,21 @@ fec_status cluster_locked(fec_ctx *ctx, const float *xyz, int64_t n, float d, in
     const Params prm = make_params((uint32_t)n, d);
     fec_status s = ensure_workspace(ctx, (size_t)n, prm.slab_cap);
     if (s != FEC_OK) return s;
+    // The boundary-edge and pair lists hold 2 entries per point; a cloud that
+    // needs more (it is reported by the device) is re-run with larger lists.
+    for (int attempt = 0;; ++attempt) {
+        s = cluster_once(ctx, xyz, n, d, min_size, max_size, labels, num_clusters, prm);
+        if (!(ctx->summary_host->status & ST_QUEUE_OVERFLOW) || attempt == 3) return s;
+        ctx->ws.list_scale *= 4;
+        s = ensure_workspace(ctx, (size_t)n, prm.slab_cap, true);
+        if (s != FEC_OK) return s;
+    }
+}
+
+fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+                        int64_t max_size, int32_t *labels, int32_t *num_clusters,
+                        const Params &prm)
+{
     Workspace &ws = ctx->ws;
     ws.trace = ctx->tracing ? &ctx->trace : nullptr;
     if (ws.trace) ws.trace->begin(ctx->stream);
@@ -450,6 +485,7 @@ int64_t fec_workspace_bytes(int64_t n, float d)
     if (n < 0 || !std::isfinite(d) || !(d > 0.0f)) return -1;
     const Params prm = make_params((uint32_t)n, d);
     Workspace probe;
+    probe.sms = 160;  // estimate for a device not yet opened
     return (int64_t)workspace_layout(probe, nullptr, (size_t)(n < 4096 ? 4096 : n), prm.slab_cap);
 }
 

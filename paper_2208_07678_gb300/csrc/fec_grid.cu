@@ -53,6 +53,9 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->union_counter = 0;
         plan->pairq_n = 0;
         plan->local_counter = 0;
+        plan->use_cols = 0;
+        plan->edges_n = 0;
+        plan->region_counter = 0;
         plan->sort.n = n;
         plan->sort.npasses = 0;
         plan->sort.key64 = 0;
@@ -159,6 +162,7 @@ __global__ void k_plan(Plan *plan, Params prm)
         return;
     }
     plan->key_bits = total + 3;
+    plan->use_cols = (plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
     plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
     plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
 }
@@ -520,17 +524,40 @@ __global__ void __launch_bounds__(256)
 }
 
 // a3: slab index over the major cell coordinate: cells of slab x occupy
-// [slab_lo[x], slab_hi[x]) of the sorted cell array (empty: lo == hi == 0).
+// [slab_lo[x], slab_hi[x]) of the sorted cell array (empty: lo == hi == 0);
+// and, when it fits, the dense column index over (c_p0, c_p1) the same way.
+__global__ void __launch_bounds__(256)
+    k_clear_cols(Plan *plan, uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi)
+{
+    if (!plan->use_cols) return;
+    const size_t ncol = (size_t)1 << (plan->bits[0] + plan->bits[1]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ncol;
+         i += (size_t)gridDim.x * blockDim.x) {
+        col_lo[i] = 0;
+        col_hi[i] = 0;
+    }
+}
+
 __global__ void __launch_bounds__(256)
     k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
-            uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi)
+            uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
+            uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi)
 {
     const uint32_t M = plan->M_c;
-    const uint32_t sh = plan->bits[1] + plan->bits[2];
+    const uint32_t b2 = plan->bits[2];
+    const uint32_t sh = plan->bits[1] + b2;
+    const bool cols = plan->use_cols != 0;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
-        const unsigned long long x = cell_key[c] >> sh;
-        if (c == 0 || (cell_key[c - 1] >> sh) != x) slab_lo[x] = c;
-        if (c + 1 == M || (cell_key[c + 1] >> sh) != x) slab_hi[x] = c + 1;
+        const unsigned long long k = cell_key[c];
+        const unsigned long long x = k >> sh, col = k >> b2;
+        const unsigned long long kp = c > 0 ? cell_key[c - 1] : ~0ull;
+        const unsigned long long kn = c + 1 < M ? cell_key[c + 1] : ~0ull;
+        if (c == 0 || (kp >> sh) != x) slab_lo[x] = c;
+        if (c + 1 == M || (kn >> sh) != x) slab_hi[x] = c + 1;
+        if (cols) {
+            if (c == 0 || (kp >> b2) != col) col_lo[col] = c;
+            if (c + 1 == M || (kn >> b2) != col) col_hi[col] = c + 1;
+        }
     }
 }
 
@@ -577,7 +604,9 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     e = cudaMemsetAsync(ws.slab_hi, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_slabs", st);
-    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.slab_lo, ws.slab_hi);
+    k_clear_cols<<<grid, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
+    FEC_MARK(ws, "k_clear_cols", st);
+    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.slab_lo, ws.slab_hi, ws.col_lo, ws.col_hi);
     FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ enum : uint32_t {
     ST_WAIT_TIMEOUT = 1u << 3,     // a look-back wait hit its cap
     ST_UNION_CAP = 1u << 4,        // a union/find loop hit its cap
     ST_SIZE_OVERFLOW = 1u << 5,    // a device count exceeded its buffer
+    ST_QUEUE_OVERFLOW = 1u << 6,   // more boundary edges / pairs than the lists hold
 };
 
 // Work counters of the union step (Plan::ctr).
@@ -54,6 +55,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
 constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a block
+constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept per block
+constexpr uint32_t kRegionCellsPerBlock = 1024;
 constexpr uint32_t kWaitCap = 1u << 22;  // spin iterations before a wait gives up
 constexpr uint32_t kUnionCap = 1u << 20; // retries of one union before it gives up
 
@@ -80,7 +83,9 @@ struct Plan {
     uint32_t union_counter;     // dynamic cell chunks of the union step
     uint32_t pairq_n;           // pairs queued for point-level tests
     uint32_t local_counter;     // dynamic cell chunks of the in-cell step
-    uint32_t pad2[3];
+    uint32_t use_cols;          // 1: the dense column index covers the grid
+    uint32_t edges_n;           // boundary edges emitted by the neighbour step
+    uint32_t region_counter;    // dynamic regions of the neighbour step
     unsigned long long ctr[8];  // work counters of the union step (CTR_*)
     SortCtl sort;              // main (key, index) sort
     SortCtl kept;              // sort of kept components by smallest index
@@ -94,6 +99,7 @@ struct Params {
     int32_t h;           // sub-cell side (units); cells have side S = 2h
     int32_t S;
     uint32_t slab_cap;   // entries of the slab index (>= max major cell coordinate + 1)
+    uint32_t col_bits;   // log2 of the dense column index capacity
 };
 
 // Quantised point record in cell order: coordinates and the original index.
@@ -248,7 +254,16 @@ struct Workspace {
     uint32_t *slab_hi = nullptr;
     uint2 *pairq = nullptr;        // sub-cell pairs queued for point tests
     Rec *reps = nullptr;           // per sub-cell: its point nearest the box centre
-    uint32_t *lroot = nullptr;     // per sub-cell: smallest sub-cell of its in-cell component
+    uint32_t *col_lo = nullptr;    // dense column index: cells of column (c0, c1) are
+    uint32_t *col_hi = nullptr;    //   [col_lo, col_hi) of the sorted cell array
+    uint32_t col_bits = 0;         // log2 of its capacity
+    uint2 *edges = nullptr;        // boundary edges of the neighbour step
+    size_t edges_cap = 0;
+    uint32_t *nb_first = nullptr;  // per cell: first sub-cell of each neighbour cell (13)
+    uint8_t *nb_cnt = nullptr;     // per cell: sub-cell count of each neighbour, K in byte 15
+    uint32_t *scratch = nullptr;   // per block of the neighbour step: undecided in-region pairs
+    size_t scratch_words = 0;
+    uint32_t list_scale = 1;       // boundary-edge and pair lists hold list_scale * 2 * cap_n
     size_t pairq_cap = 0;
     // The kept-component sort reuses the key buffers once the cell table is built.
     uint32_t *kept_key_a() const { return (uint32_t *)keys_a; }
@@ -261,6 +276,15 @@ struct Workspace {
 // (no-op unless tracing is enabled).
 void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
 #define FEC_MARK(ws, name, st) trace_mark((ws), (name), (st))
+
+// Blocks of the region kernel for n points (at most 3 per SM, at most one per
+// possible region).
+inline uint32_t region_grid(const Workspace &ws, uint64_t n)
+{
+    const uint64_t regions = (n + kRegionCellsPerBlock - 1) / kRegionCellsPerBlock;
+    const uint64_t g = (uint64_t)ws.sms * 3;
+    return (uint32_t)(regions < g ? (regions ? regions : 1) : g);
+}
 
 // Bytes of a workspace for cap_n points and slab_cap slab entries; with a
 // non-null base, also carves the arrays into ws.

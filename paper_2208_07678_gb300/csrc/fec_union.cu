@@ -23,7 +23,6 @@ namespace {
 
 constexpr int kUnionThreads = 256;
 constexpr int kUnionWarps = kUnionThreads / 32;
-constexpr int kUnionChunk = 4;
 
 // Squared distance of an offset, compared against T2.  Narrow form: each
 // |component| is clamped to R+1 (anything above R already fails the test),
@@ -189,290 +188,464 @@ __device__ __forceinline__ int box_decide(const SubBox &A, const SubBox &B, cons
     return 2;
 }
 
-// Pairs (ia < ib) of the up to 8 sub-cells of one cell.
-__constant__ uint8_t kPairA[28] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2,
-                                   2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
-__constant__ uint8_t kPairB[28] = {1, 2, 3, 4, 5, 6, 7, 2, 3, 4, 5, 6, 7, 3,
-                                   4, 5, 6, 7, 4, 5, 6, 7, 5, 6, 7, 6, 7, 7};
-
-// Hand out cells in chunks (dynamic schedule: work per cell varies by
-// orders of magnitude between sparse and dense regions).
-struct CellSchedule {
-    uint32_t base = 0, left = 0;
-    __device__ __forceinline__ bool next(uint32_t *counter, uint32_t M, uint32_t &c)
-    {
-        for (;;) {
-            if (left == 0) {
-                uint32_t got = 0;
-                if ((threadIdx.x & 31) == 0) got = atomicAdd(counter, (uint32_t)kUnionChunk);
-                base = __shfl_sync(0xffffffffu, got, 0);
-                left = kUnionChunk;
-                if (base >= M) return false;
-            }
-            c = base++;
-            --left;
-            if (c < M) return true;
-            left = 0;
-        }
-    }
-};
-
-// a4, first half: components inside each cell.  A warp takes a cell, decides
-// its <= 28 sub-cell pairs (boxes, representatives, then point tests) with a
-// warp-local union-find, and writes lroot = parent = the smallest sub-cell of
-// each in-cell component.  No global atomics on the union-find.
-template <bool WIDE>
-__global__ void __launch_bounds__(kUnionThreads, 4)
-    k_local(Plan *plan, Params prm, const uint32_t *__restrict__ cell_sc,
-            const SubBox *__restrict__ box, const Rec *__restrict__ reps,
-            const Rec *__restrict__ rec, uint32_t *__restrict__ parent,
-            uint32_t *__restrict__ lroot)
+// Cells of column (n0, n1) with minor coordinate in [z_lo, z_hi] (at most
+// 3): through the dense column index when the plan enables it, else by
+// binary search in slab n0.  Returns how many were written to out[].
+__device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long long n1,
+                                            unsigned long long z_lo, unsigned long long z_hi,
+                                            uint32_t b1, uint32_t b2, const Plan *plan,
+                                            uint32_t slab_cap,
+                                            const unsigned long long *__restrict__ cell_key,
+                                            const uint32_t *__restrict__ slab_lo,
+                                            const uint32_t *__restrict__ slab_hi,
+                                            const uint32_t *__restrict__ col_lo,
+                                            const uint32_t *__restrict__ col_hi, uint32_t out[3])
 {
-    __shared__ SubBox s_box[kUnionWarps][8];
-    __shared__ Rec s_rep[kUnionWarps][8];
-    __shared__ uint8_t s_lp[kUnionWarps][8];
-    const uint32_t M = plan->M_c;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Metric<WIDE> m;
-    m.T2 = (typename Metric<WIDE>::T)prm.T2;
-    m.R1 = prm.R + 1;
-    unsigned long long n_pairs = 0, n_yes = 0, n_tests = 0, n_evals = 0;
-    CellSchedule sched;
-    uint32_t c;
-    while (sched.next(&plan->local_counter, M, c)) {
-        const uint32_t a_lo = cell_sc[c], na = cell_sc[c + 1] - a_lo;
-        if (na == 1) {
-            if (lane == 0) lroot[a_lo] = a_lo;
-            continue;
-        }
-        if (lane < (int)na) {
-            s_box[w][lane] = box[a_lo + lane];
-            s_rep[w][lane] = reps[a_lo + lane];
-            s_lp[w][lane] = (uint8_t)lane;
-        }
-        __syncwarp();
-        int dec = 0;
-        const int ia = lane < 28 ? kPairA[lane] : 0, ib = lane < 28 ? kPairB[lane] : 0;
-        if (lane < 28 && ib < (int)na)
-            dec = box_decide<WIDE>(s_box[w][ia], s_box[w][ib], s_rep[w][ia], s_rep[w][ib], m);
-        const uint32_t yes = __ballot_sync(0xffffffffu, dec == 1);
-        uint32_t und = __ballot_sync(0xffffffffu, dec == 2);
-        n_pairs += na * (na - 1) / 2;
-        n_yes += __popc(yes);
-        n_tests += __popc(und);
-        // local union-find over <= 8 entries, kept by lane 0 (root = smallest)
-        if (lane == 0) {
-            for (uint32_t y = yes; y; y &= y - 1) {
-                const int p = __ffs(y) - 1;
-                int x = kPairA[p], z = kPairB[p];
-                while (s_lp[w][x] != x) x = s_lp[w][x];
-                while (s_lp[w][z] != z) z = s_lp[w][z];
-                if (x != z) s_lp[w][max(x, z)] = (uint8_t)min(x, z);
-            }
-        }
-        __syncwarp();
-        while (und) {
-            const int p = __ffs(und) - 1;
-            und &= und - 1;
-            int x = kPairA[p], z = kPairB[p];
-            while (s_lp[w][x] != x) x = s_lp[w][x];
-            while (s_lp[w][z] != z) z = s_lp[w][z];
-            if (x == z) continue;  // warp-uniform: s_lp is read by every lane
-            if (warp_pair_test<WIDE>(a_lo + kPairA[p], a_lo + kPairB[p], box, rec, m, n_evals)) {
-                if (lane == 0) s_lp[w][max(x, z)] = (uint8_t)min(x, z);
-            }
-            __syncwarp();
-        }
-        if (lane < (int)na) {
-            int x = lane;
-            while (s_lp[w][x] != x) x = s_lp[w][x];
-            lroot[a_lo + lane] = a_lo + x;
-            parent[a_lo + lane] = a_lo + x;
-        }
-        __syncwarp();
+    uint32_t lo, end;
+    if (plan->use_cols) {
+        const unsigned long long col = (n0 << b1) | n1;
+        lo = col_lo[col];
+        end = col_hi[col];
+    } else {
+        if (n0 >= slab_cap) return 0;
+        lo = slab_lo[n0];
+        end = slab_hi[n0];
     }
-    n_yes = __reduce_add_sync(0xffffffffu, (uint32_t)(lane == 0 ? n_yes : 0));
-    if (lane == 0) {
-        atomicAdd(&plan->ctr[CTR_PAIRS], n_pairs);
-        atomicAdd(&plan->ctr[CTR_BOX_JOINS], n_yes);
-        atomicAdd(&plan->ctr[CTR_POINT_TESTS], n_tests);
-        atomicAdd(&plan->ctr[CTR_POINT_EVALS], n_evals);
+    const unsigned long long colkey = (n0 << (b1 + b2)) | (n1 << b2);
+    const unsigned long long tlo = colkey | z_lo, thi = colkey | z_hi;
+    uint32_t hi = end;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cell_key[mid] < tlo) lo = mid + 1;
+        else hi = mid;
+    }
+    int k = 0;
+    for (uint32_t q = lo; q < end && k < 3; ++q) {
+        if (cell_key[q] > thi) break;
+        out[k++] = q;
+    }
+    return k;
+}
+
+// The half-stencil neighbour cells of cell c (13 of the 26; the other half
+// is covered by the neighbours' own visits), one column per lane: lanes
+// 0..3 take columns (0,+1), (+1,-1), (+1,0), (+1,+1) over dz in {-1,0,+1},
+// lane 4 takes (0,0,+1), the next cell of the same column.  Each lane
+// returns its cells in f[0..2] and their count.
+__device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, unsigned long long ck,
+                                            uint32_t b1, uint32_t b2, const Plan *plan,
+                                            uint32_t slab_cap,
+                                            const unsigned long long *__restrict__ cell_key,
+                                            const uint32_t *__restrict__ slab_lo,
+                                            const uint32_t *__restrict__ slab_hi,
+                                            const uint32_t *__restrict__ col_lo,
+                                            const uint32_t *__restrict__ col_hi, uint32_t f[3])
+{
+    const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
+    const unsigned long long c0 = ck >> (b1 + b2), c1 = (ck >> b2) & m1, c2 = ck & m2;
+    if (lane == 4) {
+        if (c2 < m2 && c + 1 < M && cell_key[c + 1] == ck + 1) {
+            f[0] = c + 1;
+            return 1;
+        }
+        return 0;
+    }
+    if (lane > 3) return 0;
+    const long long d0 = lane == 0 ? 0 : 1;
+    const long long d1 = lane == 0 ? 1 : lane - 2;
+    const long long n0 = (long long)c0 + d0, n1 = (long long)c1 + d1;
+    const unsigned long long m0 = (1ull << plan->bits[0]) - 1;
+    if (n1 < 0 || (unsigned long long)n1 > m1 || (unsigned long long)n0 > m0) return 0;
+    return column_cells((unsigned long long)n0, (unsigned long long)n1, c2 > 0 ? c2 - 1 : 0,
+                        c2 < m2 ? c2 + 1 : m2, b1, b2, plan, slab_cap, cell_key, slab_lo, slab_hi,
+                        col_lo, col_hi, f);
+}
+
+// ceil(65536 / n) for n = 1..8: i / n == (i * kRecip[n]) >> 16 for i < 8192.
+__constant__ uint32_t kRecip[9] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192};
+
+// a4: half-stencil neighbour lists, one thread per cell: for each of the
+// cell's K <= 13 neighbour cells, its first sub-cell and sub-cell count.
+//   nb_first[c * 13 + k], nb_cnt[c * 16 + k] (k < K), nb_cnt[c * 16 + 15] = K
+__global__ void __launch_bounds__(256, 4)
+    k_nbrs(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
+           const uint32_t *__restrict__ cell_sc, const uint32_t *__restrict__ slab_lo,
+           const uint32_t *__restrict__ slab_hi, const uint32_t *__restrict__ col_lo,
+           const uint32_t *__restrict__ col_hi, uint32_t *__restrict__ nb_first,
+           uint8_t *__restrict__ nb_cnt)
+{
+    const uint32_t M = plan->M_c;
+    const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        const unsigned long long ck = cell_key[c];
+        uint32_t cnt[16];
+        int K = 0;
+#pragma unroll
+        for (int col = 0; col < 5; ++col) {
+            uint32_t f[3];
+            const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, b1, b2, plan, prm.slab_cap,
+                                        cell_key, slab_lo, slab_hi, col_lo, col_hi, f);
+            for (int t = 0; t < nf; ++t) {
+                const uint32_t q = f[t], first = cell_sc[q];
+                nb_first[(size_t)c * 13 + K] = first;
+                cnt[K] = cell_sc[q + 1] - first;
+                ++K;
+            }
+        }
+        uint32_t wv[4] = {0, 0, 0, 0};
+        for (int k = 0; k < K; ++k) wv[k >> 2] |= cnt[k] << (8 * (k & 3));
+        wv[3] |= (uint32_t)K << 24;
+        reinterpret_cast<uint4 *>(nb_cnt)[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     }
 }
 
-// a4, second half: pairs across neighbouring cells.  A warp takes a cell,
-// finds its half-stencil neighbour cells (13 of the 26; the other half is
-// covered by the neighbours' own visits) through the slab index, and decides
-// every sub-cell pair (a in the cell, b in a neighbour) from boxes and
-// representatives.  Pairs are grouped by in-cell component pair
-// (lroot[a], lroot[b]): a group with any decided edge joins the two
-// components once; a group with only undecided pairs checks the global roots
-// once and, if they differ, queues its pairs for k_pairs.
-template <bool WIDE>
-__global__ void __launch_bounds__(kUnionThreads, 4)
-    k_global(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
-             const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
-             const Rec *__restrict__ reps, const Rec *__restrict__ rec,
-             const uint32_t *__restrict__ lroot, uint32_t *parent,
-             const uint32_t *__restrict__ slab_lo, const uint32_t *__restrict__ slab_hi,
-             uint2 *__restrict__ pairq, uint32_t qcap)
-{
-    __shared__ uint32_t s_nb[kUnionWarps][16];
-    __shared__ uint32_t s_pre[kUnionWarps][17];
-    __shared__ SubBox s_box[kUnionWarps][8];
-    __shared__ Rec s_rep[kUnionWarps][8];
-    __shared__ uint32_t s_lr[kUnionWarps][8];
+// ---------------------------------------------------------------------------
+// a4: region-local connectivity.  A block takes a region of kRegionCells
+// consecutive cells (in key order, i.e. a compact piece of space) and keeps a
+// union-find over the region's sub-cells in shared memory.  Its warps take
+// the region's cells one at a time and decide sub-cell pairs 32 at a time:
+// the cell's own pairs and its half-stencil neighbour pairs (13 of the 26
+// neighbour cells; the other half is covered by the neighbours' own visits).
+//   phase A: pairs already joined in the region are skipped; box gap above
+//            d = no edge; box diameter or representatives within d = edge
+//            (joined in shared memory, or emitted as a boundary edge when
+//            the neighbour lies in another region);
+//   phase B: the undecided pairs still apart: inside the region a warp tests
+//            points (witness search) and joins on a hit; across regions
+//            they are queued for k_pairs;
+//   phase C: every sub-cell's global parent = its region-local root.
+// Only boundary edges and cross-region pairs leave the block, through
+// shared-memory buffers flushed in chunks.
+// ---------------------------------------------------------------------------
+constexpr int kRegionCells = (int)kRegionCellsPerBlock;
+constexpr int kRegionSubs = 8 * kRegionCells;
+constexpr int kRegionBuf = 512;
 
+struct RegionSmem {
+    uint32_t par[kRegionSubs];
+    uint2 ebuf[kRegionBuf];   // boundary edges
+    uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
+    uint32_t ecount, qcount, next, region, scount, pad[3];
+    uint32_t nbl[kUnionWarps][16];
+    uint32_t pre[kUnionWarps][16];
+    uint8_t kof[kUnionWarps][112];
+    SubBox sbox[kUnionWarps][8];
+    Rec srep[kUnionWarps][8];
+};
+
+__device__ __forceinline__ uint32_t s_find(volatile uint32_t *par, uint32_t x)
+{
+    for (;;) {
+        const uint32_t p = par[x];
+        if (p == x) return x;
+        const uint32_t g = par[p];
+        if (g == p) return p;
+        par[x] = g;  // path halving (g is an ancestor of x)
+        x = g;
+    }
+}
+
+__device__ __forceinline__ void s_unite(uint32_t *par, uint32_t a, uint32_t b)
+{
+    volatile uint32_t *vp = par;
+    for (;;) {
+        a = s_find(vp, a);
+        b = s_find(vp, b);
+        if (a == b) return;
+        if (a < b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        const uint32_t old = atomicCAS(par + a, a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// Warp-aggregated append of the lanes in `mask` to a shared-memory buffer;
+// when the buffer is full the entries go straight to the global list (or,
+// if that is full too, are handled by `overflow`).  Unused buffer slots keep
+// the sentinel written at block start.
+template <typename F>
+__device__ __forceinline__ void buf_append(uint32_t mask, bool mine, uint2 v, uint2 *sbuf,
+                                           uint32_t *scount, uint2 *glist, uint32_t *gcount,
+                                           uint32_t gcap, F overflow)
+{
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    const uint32_t e = __popc(mask), rank = __popc(mask & lanemask_lt());
+    uint32_t slot = 0;
+    if (lane == leader) slot = atomicAdd(scount, e);
+    slot = __shfl_sync(0xffffffffu, slot, leader);
+    if (slot + e <= (uint32_t)kRegionBuf) {
+        if (mine) sbuf[slot + rank] = v;
+        return;
+    }
+    uint32_t g = 0;
+    if (lane == leader) g = atomicAdd(gcount, e);
+    g = __shfl_sync(0xffffffffu, g, leader);
+    if (mine) {
+        if (g + rank < gcap) glist[g + rank] = v;
+        else overflow(v);
+    }
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kUnionThreads, 3)
+    k_region(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
+             const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
+             const Rec *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
+             const uint32_t *__restrict__ nb_first, const uint8_t *__restrict__ nb_cnt,
+             uint2 *__restrict__ pairq, uint32_t qcap, uint2 *__restrict__ edges, uint32_t ecap,
+             uint32_t *__restrict__ scratch, uint32_t scap)
+{
+    extern __shared__ __align__(16) unsigned char region_smem[];
+    RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
     const uint32_t M = plan->M_c;
-    const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
-    const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nregions = (M + kRegionCells - 1) / kRegionCells;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     uint32_t *status = &plan->status;
     Metric<WIDE> m;
     m.T2 = (typename Metric<WIDE>::T)prm.T2;
     m.R1 = prm.R + 1;
+    uint32_t n_pairs = 0, n_yes = 0, n_und = 0, n_same = 0, n_queued = 0, n_edges = 0;
+    unsigned long long n_evals = 0;
+    volatile uint32_t *vpar = S.par;
+    // this block's list of undecided in-region pairs (local indices a | b << 16
+    // would not fit 8192 sub-cells twice, so two u16 halves of a u32: a, b < 8192)
+    uint32_t *const my_scratch = scratch + (size_t)blockIdx.x * scap;
 
-    unsigned long long n_pairs = 0, n_yes = 0, n_tests = 0, n_same = 0, n_queued = 0;
-    CellSchedule sched;
-    uint32_t c;
-    while (sched.next(&plan->union_counter, M, c)) {
-        const unsigned long long ck = cell_key[c];
-        const unsigned long long c0 = ck >> (b1 + b2);
-        const unsigned long long c1 = (ck >> b2) & m1, c2 = ck & m2;
-        const uint32_t a_lo = cell_sc[c], na = cell_sc[c + 1] - a_lo;
-        if (lane < (int)na) {
-            s_box[w][lane] = box[a_lo + lane];
-            s_rep[w][lane] = reps[a_lo + lane];
-            s_lr[w][lane] = lroot[a_lo + lane];
-        }
+    // Global lists full (more boundary pairs than points): report instead of
+    // joining here, which would race with other blocks' phase C.
+    auto edge_overflow = [&](uint2) { atomicOr(status, ST_QUEUE_OVERFLOW); };
+    auto pair_overflow = [&](uint2) { atomicOr(status, ST_QUEUE_OVERFLOW); };
 
-        // Neighbour cells of the half stencil.  Lanes 0..3 search columns
-        // (0,+1), (+1,-1), (+1,0), (+1,+1) over dz in {-1,0,+1}; lane 4
-        // checks (0,0,+1), the next cell of the same column.
-        uint32_t f0 = 0, f1 = 0, f2 = 0;  // found neighbour cells (registers)
-        int nf = 0;
-        if (lane < 4) {
-            const long long d0 = lane == 0 ? 0 : 1;
-            const long long d1 = lane == 0 ? 1 : lane - 2;
-            const long long n0 = (long long)c0 + d0, n1 = (long long)c1 + d1;
-            if (n1 >= 0 && (unsigned long long)n1 <= m1 && (unsigned long long)n0 < prm.slab_cap) {
-                uint32_t lo = slab_lo[n0];
-                const uint32_t end = slab_hi[n0];
-                uint32_t hi = end;
-                const unsigned long long col = ((unsigned long long)n0 << (b1 + b2)) |
-                                               ((unsigned long long)n1 << b2);
-                const unsigned long long tlo = col | (c2 > 0 ? c2 - 1 : 0);
-                const unsigned long long thi = col | (c2 < m2 ? c2 + 1 : m2);
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (cell_key[mid] < tlo) lo = mid + 1;
-                    else hi = mid;
-                }
-                for (uint32_t q = lo; q < end && nf < 3; ++q) {
-                    if (cell_key[q] > thi) break;
-                    if (nf == 0) f0 = q;
-                    else if (nf == 1) f1 = q;
-                    else f2 = q;
-                    ++nf;
-                }
-            }
-        } else if (lane == 4) {
-            if (c2 < m2 && c + 1 < M && cell_key[c + 1] == ck + 1) {
-                f0 = c + 1;
-                nf = 1;
-            }
+    for (;;) {
+        if (tid == 0) S.region = atomicAdd(&plan->region_counter, 1u);
+        __syncthreads();
+        const uint32_t r = S.region;
+        if (r >= nregions) break;
+        const uint32_t c_lo = r * kRegionCells, c_hi = min(c_lo + kRegionCells, M);
+        const uint32_t s0 = cell_sc[c_lo], s1 = cell_sc[c_hi], ns = s1 - s0;
+        for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = i;
+        for (int i = tid; i < kRegionBuf; i += blockDim.x) {
+            S.ebuf[i] = make_uint2(0xffffffffu, 0xffffffffu);
+            S.qbuf[i] = make_uint2(0xffffffffu, 0xffffffffu);
         }
-        int incl = nf;
+        if (tid == 0) {
+            S.ecount = 0;
+            S.qcount = 0;
+            S.next = c_lo;
+        }
+        __syncthreads();
+
+        if (tid == 0) S.scount = 0;
+        __syncthreads();
+        // phase A: decide every pair once
+        for (;;) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&S.next, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= c_hi) break;
+            const uint32_t a_lo = cell_sc[c], na = cell_sc[c + 1] - a_lo;
+            if (lane < (int)na) {
+                S.sbox[w][lane] = box[a_lo + lane];
+                S.srep[w][lane] = reps[a_lo + lane];
+            }
+            // neighbour list: counts of up to 13 neighbours (+ K in byte 15)
+            const uint32_t cw = lane < 4 ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 4 + lane] : 0u;
+            const int K = (int)(__shfl_sync(0xffffffffu, cw, 3) >> 24);
+            const uint32_t cword = __shfl_sync(0xffffffffu, cw, (lane >> 2) & 3);
+            const uint32_t cnt = lane < K ? (cword >> (8 * (lane & 3))) & 255u : 0u;
+            const uint32_t first = lane < K ? nb_first[(size_t)c * 13 + lane] : 0u;
+            uint32_t ci = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        const int K = __shfl_sync(0xffffffffu, incl, 31);
-        if (nf > 0) s_nb[w][incl - nf] = f0;
-        if (nf > 1) s_nb[w][incl - nf + 1] = f1;
-        if (nf > 2) s_nb[w][incl - nf + 2] = f2;
-        __syncwarp();
-        uint32_t cnt = 0;
-        if (lane < K) {
-            const uint32_t q = s_nb[w][lane];
-            cnt = cell_sc[q + 1] - cell_sc[q];
-        }
-        uint32_t ci = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, ci, o);
-            if (lane >= o) ci += u;
-        }
-        if (lane <= K) s_pre[w][lane] = ci - cnt;  // lane K holds the total
-        __syncwarp();
-        const uint32_t T = s_pre[w][K];
-        const uint32_t P = na * T;
-        n_pairs += P;
-
-        for (uint32_t base = 0; base < P; base += 32) {
-            const uint32_t i = base + lane;
-            int dec = 0;
-            uint32_t a = 0, b = 0;
-            unsigned long long key = 0;
-            if (i < P) {
-                const uint32_t ia = i % na, jb = i / na;
-                int k = 0;
-                while (k + 1 < K && s_pre[w][k + 1] <= jb) ++k;
-                const uint32_t q = s_nb[w][k];
-                b = cell_sc[q] + (jb - s_pre[w][k]);
-                a = a_lo + ia;
-                dec = box_decide<WIDE>(s_box[w][ia], box[b], s_rep[w][ia], reps[b], m);
-                if (dec) key = ((unsigned long long)s_lr[w][ia] << 32) | lroot[b];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, ci, o);
+                if (lane >= o) ci += u;
             }
-            const uint32_t active = __ballot_sync(0xffffffffu, dec != 0);
-            const uint32_t yes_m = __ballot_sync(0xffffffffu, dec == 1);
-            n_yes += __popc(yes_m);
-            n_tests += __popc(active & ~yes_m);
-            bool enq = false;
-            if (dec) {
-                const uint32_t peers = __match_any_sync(active, key);
-                const int leader = __ffs(peers) - 1;
-                const uint32_t ra = (uint32_t)(key >> 32), rb = (uint32_t)key;
-                if (peers & yes_m) {
-                    if (lane == leader && !uf_unite(parent, ra, rb)) atomicOr(status, ST_UNION_CAP);
-                } else {
-                    int same = 0;
-                    if (lane == leader) same = uf_find(parent, ra) == uf_find(parent, rb);
-                    same = __shfl_sync(peers, same, leader);
-                    if (same) {
-                        if (lane == leader) n_same += __popc(peers);
+            const uint32_t T = __shfl_sync(0xffffffffu, ci, 31);
+            if (lane < K) {
+                S.nbl[w][lane] = first;
+                S.pre[w][lane] = ci - cnt;
+                for (uint32_t j = ci - cnt; j < ci; ++j) S.kof[w][j] = (uint8_t)lane;
+            }
+            __syncwarp();
+            const uint32_t P0 = na * (na - 1) / 2;
+            const uint32_t P = P0 + na * T;
+            const uint32_t rcp = kRecip[na];
+
+            for (uint32_t base = 0; base < P; base += 32) {
+                const uint32_t i = base + lane;
+                int dec = 0;
+                bool local = true;
+                uint32_t ia = 0, a = 0, b = 0;
+                if (i < P) {
+                    SubBox BB;
+                    Rec RB;
+                    if (i < P0) {
+                        uint32_t rem = i, ib;
+                        ia = 0;
+                        while (rem >= na - 1 - ia) {
+                            rem -= na - 1 - ia;
+                            ++ia;
+                        }
+                        ib = ia + 1 + rem;
+                        b = a_lo + ib;
+                        a = a_lo + ia;
+                        if (s_find(vpar, a - s0) != s_find(vpar, b - s0)) {
+                            BB = S.sbox[w][ib];
+                            RB = S.srep[w][ib];
+                            dec = 3;  // decide below
+                        } else {
+                            ++n_same;
+                        }
                     } else {
-                        enq = true;
+                        const uint32_t j = i - P0;
+                        const uint32_t jb = (j * rcp) >> 16;
+                        ia = j - jb * na;
+                        const uint32_t k = S.kof[w][jb];
+                        b = S.nbl[w][k] + (jb - S.pre[w][k]);
+                        a = a_lo + ia;
+                        local = b >= s0 && b < s1;
+                        if (!local || s_find(vpar, a - s0) != s_find(vpar, b - s0)) {
+                            BB = box[b];
+                            RB = reps[b];
+                            dec = 3;
+                        } else {
+                            ++n_same;
+                        }
+                    }
+                    if (dec == 3) {
+                        ++n_pairs;
+                        dec = box_decide<WIDE>(S.sbox[w][ia], BB, S.srep[w][ia], RB, m);
                     }
                 }
-            }
-            const uint32_t qmask = __ballot_sync(0xffffffffu, enq);
-            if (qmask) {
-                n_queued += __popc(qmask);
-                const int leader = __ffs(qmask) - 1;
-                uint32_t slot = 0;
-                if (lane == leader) slot = atomicAdd(&plan->pairq_n, (uint32_t)__popc(qmask));
-                slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(qmask & lanemask_lt());
-                if (enq) {
-                    if (slot < qcap) {
-                        pairq[slot] = make_uint2(a, b);
-                    } else if (thread_pair_test<WIDE>(a, b, box, rec, m)) {
-                        // queue full: decide this pair alone (slow, but exact)
-                        if (!uf_unite(parent, a, b)) atomicOr(status, ST_UNION_CAP);
+                if (dec == 1 && local) {
+                    ++n_yes;
+                    s_unite(S.par, a - s0, b - s0);
+                }
+                const bool emit = dec == 1 && !local;
+                n_edges += emit ? 1 : 0;
+                buf_append(__ballot_sync(0xffffffffu, emit), emit, make_uint2(a, b), S.ebuf,
+                           &S.ecount, edges, &plan->edges_n, ecap, edge_overflow);
+                const bool und = dec == 2;
+                n_und += und ? 1 : 0;
+                const bool cross = und && !local;
+                n_queued += cross ? 1 : 0;
+                buf_append(__ballot_sync(0xffffffffu, cross), cross, make_uint2(a, b), S.qbuf,
+                           &S.qcount, pairq, &plan->pairq_n, qcap, pair_overflow);
+                // undecided pairs inside the region: the block's scratch list
+                // (or, when it is full, the global queue)
+                const bool keep = und && local;
+                const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
+                bool spill = false;
+                if (kmask) {
+                    const int leader = __ffs(kmask) - 1;
+                    uint32_t slot = 0;
+                    if (lane == leader) slot = atomicAdd(&S.scount, (uint32_t)__popc(kmask));
+                    slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(kmask & lanemask_lt());
+                    if (keep) {
+                        if (slot < scap) my_scratch[slot] = (a - s0) | ((b - s0) << 16);
+                        else spill = true;
                     }
+                }
+                // scratch full: test those pairs right here
+                uint32_t smask = __ballot_sync(0xffffffffu, spill);
+                while (smask) {
+                    const int src = __ffs(smask) - 1;
+                    smask &= smask - 1;
+                    const uint32_t pa = __shfl_sync(0xffffffffu, a, src) - s0;
+                    const uint32_t pb = __shfl_sync(0xffffffffu, b, src) - s0;
+                    if (s_find(vpar, pa) == s_find(vpar, pb)) continue;  // warp-uniform
+                    if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
+                        s_unite(S.par, pa, pb);
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // phase B: the region's undecided pairs still apart, warp witness tests
+        {
+            const uint32_t nsc = min(S.scount, scap);
+            for (uint32_t base = w * 32; base < nsc; base += kUnionWarps * 32) {
+                const uint32_t i = base + lane;
+                uint32_t la = 0, lb = 0;
+                bool live = false;
+                if (i < nsc) {
+                    const uint32_t v = my_scratch[i];
+                    la = v & 0xffffu;
+                    lb = v >> 16;
+                    live = s_find(vpar, la) != s_find(vpar, lb);
+                }
+                uint32_t lmask = __ballot_sync(0xffffffffu, live);
+                while (lmask) {
+                    const int src = __ffs(lmask) - 1;
+                    lmask &= lmask - 1;
+                    const uint32_t pa = __shfl_sync(0xffffffffu, la, src);
+                    const uint32_t pb = __shfl_sync(0xffffffffu, lb, src);
+                    // warp-uniform: every lane reads the same shared words
+                    if (s_find(vpar, pa) == s_find(vpar, pb)) continue;
+                    if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
+                        s_unite(S.par, pa, pb);
+                    __syncwarp();
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
+        // phase C: local roots become global parents; flush the buffers
+        for (uint32_t i = tid; i < ns; i += blockDim.x) parent[s0 + i] = s0 + s_find(vpar, i);
+        const uint32_t ne = min(S.ecount, (uint32_t)kRegionBuf);
+        const uint32_t nq = min(S.qcount, (uint32_t)kRegionBuf);
+        __shared__ uint32_t s_g[2];
+        if (tid == 0) {
+            s_g[0] = ne ? atomicAdd(&plan->edges_n, ne) : 0;
+            s_g[1] = nq ? atomicAdd(&plan->pairq_n, nq) : 0;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < ne; i += blockDim.x) {
+            const uint2 v = S.ebuf[i];
+            const uint32_t g = s_g[0] + i;
+            if (g < ecap) edges[g] = v;
+            else if (v.x != 0xffffffffu) edge_overflow(v);
+        }
+        for (uint32_t i = tid; i < nq; i += blockDim.x) {
+            const uint2 v = S.qbuf[i];
+            const uint32_t g = s_g[1] + i;
+            if (g < qcap) pairq[g] = v;
+            else if (v.x != 0xffffffffu) pair_overflow(v);
+        }
+        __syncthreads();
     }
-    n_same = __reduce_add_sync(0xffffffffu, (uint32_t)n_same);
+    n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
+    n_yes = __reduce_add_sync(0xffffffffu, n_yes);
+    n_und = __reduce_add_sync(0xffffffffu, n_und);
+    n_same = __reduce_add_sync(0xffffffffu, n_same);
+    n_queued = __reduce_add_sync(0xffffffffu, n_queued);
+    n_edges = __reduce_add_sync(0xffffffffu, n_edges);
     if (lane == 0) {
-        atomicAdd(&plan->ctr[CTR_PAIRS], n_pairs);
-        atomicAdd(&plan->ctr[CTR_BOX_JOINS], n_yes);
-        atomicAdd(&plan->ctr[CTR_POINT_TESTS], n_tests);
-        atomicAdd(&plan->ctr[CTR_SAME_ROOT], n_same);
-        atomicAdd(&plan->ctr[CTR_QUEUED], n_queued);
+        atomicAdd(&plan->ctr[CTR_PAIRS], (unsigned long long)n_pairs);
+        atomicAdd(&plan->ctr[CTR_BOX_JOINS], (unsigned long long)(n_yes + n_edges));
+        atomicAdd(&plan->ctr[CTR_POINT_TESTS], (unsigned long long)n_und);
+        atomicAdd(&plan->ctr[CTR_SAME_ROOT], (unsigned long long)n_same);
+        atomicAdd(&plan->ctr[CTR_QUEUED], (unsigned long long)n_queued);
+        atomicAdd(&plan->ctr[CTR_POINT_EVALS], n_evals);
+    }
+}
+
+// a4: the boundary edges found by k_region, one union per thread (full
+// occupancy hides the latency of the pointer chasing).
+__global__ void __launch_bounds__(256)
+    k_edges(Plan *plan, const uint2 *__restrict__ edges, uint32_t ecap, uint32_t *parent)
+{
+    const uint32_t ne = min(plan->edges_n, ecap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
+        const uint2 e = edges[i];
+        if (e.x == 0xffffffffu) continue;  // unused buffer slot
+        if (!uf_unite(parent, e.x, e.y)) atomicOr(&plan->status, ST_UNION_CAP);
     }
 }
 
@@ -498,7 +671,7 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
         bool live = false;
         if (i < nq) {
             pr = pairq[i];
-            live = uf_find(parent, pr.x) != uf_find(parent, pr.y);
+            live = pr.x != 0xffffffffu && uf_find(parent, pr.x) != uf_find(parent, pr.y);
             if (!live) ++n_same;
         }
         uint32_t mask = __ballot_sync(0xffffffffu, live);
@@ -620,23 +793,31 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
                           long long max_size, cudaStream_t st)
 {
     const uint32_t qcap = (uint32_t)ws.pairq_cap;
+    const uint32_t ecap = (uint32_t)ws.edges_cap;
     const bool wide = prm.R + 1 > 26754;
+    const size_t smem = sizeof(RegionSmem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_region<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_region<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_nbrs<<<ws.sms * 8, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
+                                        ws.col_lo, ws.col_hi, ws.nb_first, ws.nb_cnt);
+    FEC_MARK(ws, "k_nbrs", st);
+    const uint32_t rgrid = region_grid(ws, prm.n);
+    const uint32_t scap = kRegionScratch;
     if (!wide)
-        k_local<false><<<ws.sms * 4, kUnionThreads, 0, st>>>(ws.plan, prm, ws.cell_sc, ws.box,
-                                                             ws.reps, ws.rec, ws.parent, ws.lroot);
+        k_region<false><<<rgrid, kUnionThreads, smem, st>>>(
+            ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
+            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     else
-        k_local<true><<<ws.sms * 4, kUnionThreads, 0, st>>>(ws.plan, prm, ws.cell_sc, ws.box,
-                                                            ws.reps, ws.rec, ws.parent, ws.lroot);
-    FEC_MARK(ws, "k_local", st);
-    if (!wide)
-        k_global<false><<<ws.sms * 4, kUnionThreads, 0, st>>>(
-            ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.lroot, ws.parent,
-            ws.slab_lo, ws.slab_hi, ws.pairq, qcap);
-    else
-        k_global<true><<<ws.sms * 4, kUnionThreads, 0, st>>>(
-            ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.lroot, ws.parent,
-            ws.slab_lo, ws.slab_hi, ws.pairq, qcap);
-    FEC_MARK(ws, "k_global", st);
+        k_region<true><<<rgrid, kUnionThreads, smem, st>>>(
+            ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
+            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
+    FEC_MARK(ws, "k_region", st);
+    k_edges<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent);
+    FEC_MARK(ws, "k_edges", st);
     if (!wide)
         k_pairs<false><<<ws.sms * 2, kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                              ws.pairq, qcap);

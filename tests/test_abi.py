@@ -58,8 +58,7 @@ def test_workspace_bytes_host_only(lib):
     assert 0 < a < b
     assert fec.fec_workspace_bytes(-1, 0.5) == -1
     assert fec.fec_workspace_bytes(10, 0.0) == -1
-    # ~130 bytes per point at scale
-    assert 100 < b / 1_000_000 < 200
+    assert 100 < b / 1_000_000 < 500  # bytes per point of the device workspace
 
 
 def test_create_without_gpu_reports_cuda_error(lib):
