@@ -43,14 +43,13 @@ KERNEL_BYTES = {
     "onesweep_u32": lambda n, Ms, Mc: 16 * n,
     "k_cells_u32": lambda n, Ms, Mc: 40 * n + 4 * Ms + 12 * Mc,
     "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 56 * Ms,
-    "k_local": lambda n, Ms, Mc: 4 * Mc + 56 * Ms,
-    "k_global": lambda n, Ms, Mc: 12 * Mc + 44 * Ms,
+    "k_region": lambda n, Ms, Mc: 76 * Mc + 60 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
     "k_labels": lambda n, Ms, Mc: 12 * n,
 }
 KERNEL_SOURCE = {
     "k_bbox": "fec_grid.cu", "k_keys_u32": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
-    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_local": "fec_union.cu", "k_global": "fec_union.cu",
+    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_region": "fec_union.cu",
     "k_flatten_stats": "fec_union.cu", "k_labels": "fec_union.cu",
 }
 HOUSEKEEPING = ("memset", "h2d", "d2h", "summary")
@@ -346,7 +345,7 @@ def run_ours(args):
             "clocks": clk,
             "union_work": {k: stats[k] for k in ("pair_checks", "pair_box_joins", "pair_point_tests",
                                                  "pair_same_root", "point_evals",
-                                                 "pairs_queued")},
+                                                 "pairs_queued", "boundary_edges")},
             "trace_ms_per_step": {"total": round(step_total_ms, 4), "traced_step_ms": ms_traced,
                                   "by_kernel": breakdown},
         }

@@ -82,6 +82,7 @@ typedef struct {
     int64_t pair_same_root;   /* ... of those, skipped as already joined */
     int64_t point_evals;      /* point-level distance evaluations */
     int64_t pairs_queued;     /* pairs deferred to the warp-per-pair pass */
+    int64_t boundary_edges;   /* edges between regions, joined after the region pass */
 } fec_stats;
 
 /* Create a context on options->device (options may be NULL: device 0, no

@@ -39,6 +39,7 @@ Params make_params(uint32_t n, float d)
     p.h = (int32_t)h;
     p.S = (int32_t)(2 * h);
     p.slab_cap = (uint32_t)(((1u << 24) - 1) / (uint32_t)p.S + 2);
+    p.packed = p.S <= 1024 ? 1u : 0u;
     return p;
 }
 
@@ -85,8 +86,8 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.labels = (int32_t *)take(4 * n);
     ws.keys_a = take(8 * n);
     ws.keys_b = take(8 * n);
-    ws.vals_a = (uint32_t *)take(4 * n);
-    ws.vals_b = (uint32_t *)take(4 * n);
+    ws.vals_a = take(8 * n);
+    ws.vals_b = take(8 * n);
     ws.sort_status = (uint32_t *)take(4 * sort_status_words((uint32_t)n));
     ws.scan_status = (unsigned long long *)take(8 * (n / kScanTile + 2));
     ws.rec = (Rec *)take(sizeof(Rec) * n);
@@ -139,20 +140,19 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
 {
     Params prm = make_params(n, d);
     prm.col_bits = ws.col_bits;
-    const int sort_grid = ws.sms * 2;
+    const int sort_grid = ws.sms;  // per SM; the sort multiplies by its occupancy
     cudaError_t e = enqueue_front(ws, xyz, prm, st);
     if (e != cudaSuccess) return e;
     // a2: both key widths are enqueued; the plan enables one of them.
-    e = launch_sort_u32(ws, "onesweep_u32", &ws.plan->sort, (uint32_t *)ws.keys_a, ws.vals_a,
-                        (uint32_t *)ws.keys_b, ws.vals_b, true, ws.sort_status, n, 4, sort_grid, st,
-                        &ws.plan->status);
+    const bool pk = prm.packed != 0;
+    e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b, ws.vals_b,
+                    false, pk, !pk, ws.sort_status, n, 4, sort_grid, st, &ws.plan->status);
     if (e != cudaSuccess) return e;
     const int p64 = max_sort_passes(prm);
     if (p64 > 4) {
-        e = launch_sort_u64(ws, "onesweep_u64", &ws.plan->sort, (unsigned long long *)ws.keys_a,
-                            ws.vals_a,
-                            (unsigned long long *)ws.keys_b, ws.vals_b, true, ws.sort_status, n,
-                            p64, sort_grid, st, &ws.plan->status);
+        e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
+                        ws.vals_b, true, pk, !pk, ws.sort_status, n, p64, sort_grid, st,
+                        &ws.plan->status);
         if (e != cudaSuccess) return e;
     }
     e = enqueue_cells(ws, xyz, prm, st);
@@ -164,13 +164,12 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
         e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), ws.sms * 4, st);
         if (e != cudaSuccess) return e;
         FEC_MARK(ws, "hist_kept", st);
-        e = launch_sort_u32(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
-                            ws.kept_key_b(),
-                            ws.kept_val_b(), false, ws.sort_status, n, kp, sort_grid, st,
-                            &ws.plan->status);
+        e = launch_sort(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
+                        ws.kept_key_b(), ws.kept_val_b(), false, false, false, ws.sort_status, n,
+                        kp, sort_grid, st, &ws.plan->status);
         if (e != cudaSuccess) return e;
     }
-    return enqueue_labels(ws, labels, st);
+    return enqueue_labels(ws, labels, prm.packed != 0, st);
 }
 
 // Small summary of a finished call, packed on the device for one copy.
@@ -371,6 +370,7 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
     st.pair_same_root = (int64_t)s.ctr[CTR_SAME_ROOT];
     st.point_evals = (int64_t)s.ctr[CTR_POINT_EVALS];
     st.pairs_queued = (int64_t)s.ctr[CTR_QUEUED];
+    st.boundary_edges = (int64_t)s.ctr[CTR_EDGES];
     const fec_status f = status_from_bits(s.status);
     if (f == FEC_OK && num_clusters) *num_clusters = (int32_t)s.k;
     return f;

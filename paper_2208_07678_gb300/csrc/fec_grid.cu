@@ -200,12 +200,42 @@ struct GridMap {
         }
         return (k << 3) | sub;
     }
+    // Sort payload of the packed layout: the original index in the low 32
+    // bits and the point's offsets inside its cell (original axes x, y, z,
+    // 10 bits each, S <= 1024) above it.
+    __device__ __forceinline__ unsigned long long payload(const int32_t q[3], uint32_t idx) const
+    {
+        unsigned long long v = idx;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t rel = (uint32_t)(q[a] - lo[a]);
+            const uint32_t off = rel - (rel / (uint32_t)S) * (uint32_t)S;
+            v |= (unsigned long long)off << (32 + 10 * a);
+        }
+        return v;
+    }
+    // Inverse of key() + payload(): the quantised coordinates of a point.
+    __device__ __forceinline__ void unpack(unsigned long long key, unsigned long long v,
+                                           int32_t q[3]) const
+    {
+        unsigned long long ck = key >> 3;
+        uint32_t c[3];
+#pragma unroll
+        for (int p = 2; p >= 0; --p) {
+            c[perm[p]] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
+            ck >>= bits[p];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            q[a] = lo[a] + (int32_t)(c[a] * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
+    }
 };
 
 // a1: grid keys of all points, plus the digit histograms of every radix pass.
-template <typename KeyT>
+template <typename KeyT, bool PACKED>
 __global__ void __launch_bounds__(256)
-    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, KeyT *__restrict__ keys)
+    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, KeyT *__restrict__ keys,
+           unsigned long long *__restrict__ vals)
 {
     constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
     SortCtl *ctl = &plan->sort;
@@ -224,6 +254,7 @@ __global__ void __launch_bounds__(256)
         for (int a = 0; a < 3; ++a) quantize1(xyz[3 * (size_t)i + a], q[a]);
         const KeyT k = (KeyT)g.key(q);
         keys[i] = k;
+        if (PACKED) vals[i] = g.payload(q, i);
         for (int p = 0; p < np; ++p) atomicAdd(&h[p][(uint32_t)(k >> (p * kRadixBits)) & 255u], 1u);
     }
     __syncthreads();
@@ -239,10 +270,10 @@ __global__ void __launch_bounds__(256)
 //   sc_of[p]      sub-cell of sorted position p
 //   sc_start[a]   first sorted position of sub-cell a (sc_start[M_s] = n)
 //   cell_key[c]   cell key of cell c; cell_sc[c] first sub-cell of cell c
-template <typename KeyT>
+template <typename KeyT, typename ValT>
 __global__ void __launch_bounds__(kScanThreads)
-    k_cells(Plan *plan, const KeyT *__restrict__ keys_a, const uint32_t *__restrict__ vals_a,
-            const KeyT *__restrict__ keys_b, const uint32_t *__restrict__ vals_b,
+    k_cells(Plan *plan, Params prm, const KeyT *__restrict__ keys_a, const ValT *__restrict__ vals_a,
+            const KeyT *__restrict__ keys_b, const ValT *__restrict__ vals_b,
             const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
             uint32_t *__restrict__ sc_start, unsigned long long *__restrict__ cell_key,
             uint32_t *__restrict__ cell_sc, unsigned long long *__restrict__ tstat)
@@ -254,7 +285,10 @@ __global__ void __launch_bounds__(kScanThreads)
     if (n == 0) return;
     const bool in_b = (ctl->npasses & 1u) != 0;
     const KeyT *__restrict__ keys = in_b ? keys_b : keys_a;
-    const uint32_t *__restrict__ vals = in_b ? vals_b : vals_a;
+    const ValT *__restrict__ vals = in_b ? vals_b : vals_a;
+    constexpr bool PACKED = sizeof(ValT) == 8;
+    GridMap g;
+    if (PACKED) g.load(plan, prm);
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
 
     constexpr unsigned long long kAgg = 1ull << 62, kIncl = 2ull << 62;
@@ -337,9 +371,9 @@ __global__ void __launch_bounds__(kScanThreads)
         __syncthreads();
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
 
-        uint32_t vv[kScanIPT];
+        ValT vv[kScanIPT];
 #pragma unroll
-        for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : 0u;
+        for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : (ValT)0;
         unsigned long long before = base;
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
@@ -351,7 +385,7 @@ __global__ void __launch_bounds__(kScanThreads)
             const bool sh = (cur & 0x7fffffffull) != (before & 0x7fffffffull);
             const bool ch = (cur >> 31) != (before >> 31);
             before = cur;
-            const uint32_t idx = vv[i];
+            const uint32_t idx = (uint32_t)vv[i];
             if (sc >= n || c >= n || idx >= n) {  // only after a look-back timeout
                 atomicOr(&plan->status, ST_SIZE_OVERFLOW);
                 continue;
@@ -363,9 +397,17 @@ __global__ void __launch_bounds__(kScanThreads)
                 cell_sc[c] = sc;
             }
             Rec r;
-            quantize1(xyz[3 * (size_t)idx + 0], r.x);
-            quantize1(xyz[3 * (size_t)idx + 1], r.y);
-            quantize1(xyz[3 * (size_t)idx + 2], r.z);
+            if (PACKED) {
+                int32_t q[3];
+                g.unpack((unsigned long long)k[i], (unsigned long long)vv[i], q);
+                r.x = q[0];
+                r.y = q[1];
+                r.z = q[2];
+            } else {  // gather from the input (cells wider than 1024 units)
+                quantize1(xyz[3 * (size_t)idx + 0], r.x);
+                quantize1(xyz[3 * (size_t)idx + 1], r.y);
+                quantize1(xyz[3 * (size_t)idx + 2], r.z);
+            }
             r.idx = idx;
             rec[p] = r;
             if (p == n - 1) {
@@ -570,9 +612,18 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cu
     FEC_MARK(ws, "k_bbox", st);
     k_plan<<<1, 32, 0, st>>>(ws.plan, prm);
     FEC_MARK(ws, "k_plan", st);
-    k_keys<uint32_t><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a);
-    FEC_MARK(ws, "k_keys_u32", st);
-    k_keys<unsigned long long><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (unsigned long long *)ws.keys_a);
+    auto *va = (unsigned long long *)ws.vals_a;
+    if (prm.packed) {
+        k_keys<uint32_t, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a, va);
+        FEC_MARK(ws, "k_keys_u32", st);
+        k_keys<unsigned long long, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm,
+                                                              (unsigned long long *)ws.keys_a, va);
+    } else {
+        k_keys<uint32_t, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a, va);
+        FEC_MARK(ws, "k_keys_u32", st);
+        k_keys<unsigned long long, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm,
+                                                               (unsigned long long *)ws.keys_a, va);
+    }
     FEC_MARK(ws, "k_keys_u64", st);
     return cudaGetLastError();
 }
@@ -584,14 +635,29 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_scan_status", st);
     const int grid = ws.sms * 8;
-    k_cells<uint32_t><<<grid, kScanThreads, 0, st>>>(
-        ws.plan, (const uint32_t *)ws.keys_a, ws.vals_a, (const uint32_t *)ws.keys_b, ws.vals_b, xyz,
-        ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc, ws.scan_status);
-    FEC_MARK(ws, "k_cells_u32", st);
-    k_cells<unsigned long long><<<grid, kScanThreads, 0, st>>>(
-        ws.plan, (const unsigned long long *)ws.keys_a, ws.vals_a,
-        (const unsigned long long *)ws.keys_b, ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start,
-        ws.cell_key, ws.cell_sc, ws.scan_status);
+    using u32 = uint32_t;
+    using u64 = unsigned long long;
+    if (prm.packed) {
+        k_cells<u32, u64><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, (const u32 *)ws.keys_a, (const u64 *)ws.vals_a, (const u32 *)ws.keys_b,
+            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            ws.scan_status);
+        FEC_MARK(ws, "k_cells_u32", st);
+        k_cells<u64, u64><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, (const u64 *)ws.keys_a, (const u64 *)ws.vals_a, (const u64 *)ws.keys_b,
+            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            ws.scan_status);
+    } else {
+        k_cells<u32, u32><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, (const u32 *)ws.keys_a, (const u32 *)ws.vals_a, (const u32 *)ws.keys_b,
+            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            ws.scan_status);
+        FEC_MARK(ws, "k_cells_u32", st);
+        k_cells<u64, u32><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, (const u64 *)ws.keys_a, (const u32 *)ws.vals_a, (const u64 *)ws.keys_b,
+            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            ws.scan_status);
+    }
     FEC_MARK(ws, "k_cells_u64", st);
     k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.box, ws.sminidx,
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);

@@ -43,13 +43,24 @@ enum {
     CTR_SAME_ROOT = 3,    // ... of which skipped because already joined
     CTR_POINT_EVALS = 4,  // point-level distance evaluations
     CTR_QUEUED = 5,       // pairs queued for the warp-per-pair kernel
+    CTR_EDGES = 6,        // edges between regions joined after the region step
 };
 
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;            // 64-bit keys
-constexpr int kSortThreads = 512;
-constexpr int kSortIPT = 8;              // items per thread
+#ifndef FEC_SORT_THREADS
+#define FEC_SORT_THREADS 512
+#endif
+#ifndef FEC_SORT_IPT
+#define FEC_SORT_IPT 8
+#endif
+#ifndef FEC_SORT_MINB
+#define FEC_SORT_MINB 2
+#endif
+constexpr int kSortThreads = FEC_SORT_THREADS;
+constexpr int kSortIPT = FEC_SORT_IPT;   // items per thread
+constexpr int kSortMinBlocks = FEC_SORT_MINB;
 constexpr int kSortTile = kSortThreads * kSortIPT;   // 4096 keys per tile
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
@@ -100,6 +111,7 @@ struct Params {
     int32_t S;
     uint32_t slab_cap;   // entries of the slab index (>= max major cell coordinate + 1)
     uint32_t col_bits;   // log2 of the dense column index capacity
+    uint32_t packed;     // 1: sort values carry the in-cell offsets (S <= 1024)
 };
 
 // Quantised point record in cell order: coordinates and the original index.
@@ -234,8 +246,8 @@ struct Workspace {
     int32_t *labels = nullptr;     // staging of host output
     void *keys_a = nullptr;        // 8 * cap_n bytes each (32- or 64-bit keys)
     void *keys_b = nullptr;
-    uint32_t *vals_a = nullptr;
-    uint32_t *vals_b = nullptr;
+    void *vals_a = nullptr;        // 8 * cap_n bytes each (32-bit index or 64-bit packed payload)
+    void *vals_b = nullptr;
     uint32_t *sort_status = nullptr;
     unsigned long long *scan_status = nullptr;
     Rec *rec = nullptr;
@@ -305,26 +317,22 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
 cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
                           long long max_size, cudaStream_t st);
 // a6 rank + labels (labels: device pointer, n entries).
-cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, cudaStream_t st);
+cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, bool packed, cudaStream_t st);
 // The whole pipeline for one cloud (device pointers), no host synchronisation.
 cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
                             long long min_size, long long max_size, int32_t *labels,
                             cudaStream_t st);
 
 // Onesweep radix sort of (key, value) over ctl->npasses 8-bit digits, with
-// digit histograms already in ctl->hist.  Values may be null (identity index
-// 0..n-1 for the first pass).  Kernels for the key width that ctl->key64 does
-// not select return at once, so both widths can be enqueued blindly.
-// Result lands in keys_a/vals_a if npasses is even, else keys_b/vals_b.
-cudaError_t launch_sort_u32(const Workspace &ws, const char *name, SortCtl *ctl, uint32_t *keys_a,
-                            uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
-                            bool identity_vals, uint32_t *tile_status, uint32_t max_n,
-                            int max_passes, int grid, cudaStream_t st, uint32_t *status);
-cudaError_t launch_sort_u64(const Workspace &ws, const char *name, SortCtl *ctl,
-                            unsigned long long *keys_a, uint32_t *vals_a,
-                            unsigned long long *keys_b, uint32_t *vals_b, bool identity_vals,
-                            uint32_t *tile_status, uint32_t max_n, int max_passes, int grid,
-                            cudaStream_t st, uint32_t *status);
+// digit histograms already in ctl->hist.  Keys are 32- or 64-bit, values 32-
+// or 64-bit; values may be the identity index 0..n-1 for the first pass.
+// Kernels for a key width that ctl->key64 does not select return at once, so
+// both widths can be enqueued blindly.  The result lands in keys_a/vals_a if
+// npasses is even, else in keys_b/vals_b.
+cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, void *keys_a,
+                        void *vals_a, void *keys_b, void *vals_b, bool key64, bool val64,
+                        bool identity_vals, uint32_t *tile_status, uint32_t max_n, int max_passes,
+                        int grid, cudaStream_t st, uint32_t *status);
 // uint32 words of look-back status a sort of up to max_n keys needs.
 inline size_t sort_status_words(uint32_t max_n)
 {

@@ -18,14 +18,15 @@ namespace fec {
 namespace {
 
 constexpr int kWarps = kSortThreads / 32;
+static_assert(kSortThreads >= kRadixBins, "the digit loops need one thread per digit");
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
-template <typename KeyT>
+template <typename KeyT, typename ValT>
 struct SortSmem {
     KeyT keys[kSortTile];
-    uint32_t vals[kSortTile];
+    ValT vals[kSortTile];
     uint16_t wcnt[kWarps][kRadixBins];
     uint32_t gofs[kRadixBins];   // exclusive global offset of each digit (whole pass)
     uint32_t cnt[kRadixBins];    // tile count of each digit
@@ -59,11 +60,11 @@ __device__ __forceinline__ void scan256(const uint32_t *in, uint32_t *out, uint3
     __syncthreads();
 }
 
-template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads)
+template <typename KeyT, typename ValT>
+__global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     k_onesweep(SortCtl *__restrict__ ctl, const KeyT *__restrict__ kin,
-               const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
-               uint32_t *__restrict__ vout, uint32_t *__restrict__ tstat_base, size_t tstride,
+               const ValT *__restrict__ vin, KeyT *__restrict__ kout,
+               ValT *__restrict__ vout, uint32_t *__restrict__ tstat_base, size_t tstride,
                int pass, uint32_t *__restrict__ status)
 {
     // Two look-back status arrays alternate between passes: this pass reads
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kSortThreads)
     const int shift = pass * kRadixBits;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem<KeyT> &S = *reinterpret_cast<SortSmem<KeyT> *>(smem_raw);
+    SortSmem<KeyT, ValT> &S = *reinterpret_cast<SortSmem<KeyT, ValT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     if (tid < kRadixBins) S.cnt[tid] = ctl->hist[pass][tid];
@@ -94,14 +95,15 @@ __global__ void __launch_bounds__(kSortThreads)
         if (tile >= ntiles) break;
 
         KeyT key[kSortIPT];
-        uint32_t val[kSortIPT], lrank[kSortIPT], dig[kSortIPT];
+        ValT val[kSortIPT];
+        uint32_t lrank[kSortIPT], dig[kSortIPT];
         const uint32_t seg = tile * (uint32_t)kSortTile + warp * (32u * kSortIPT);
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const uint32_t pos = seg + r * 32 + lane;
             const bool valid = pos < n;
             key[r] = valid ? kin[pos] : KeyT(0);
-            val[r] = valid ? (vin ? vin[pos] : pos) : 0u;
+            val[r] = valid ? (vin ? vin[pos] : (ValT)pos) : (ValT)0;
             const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRadixBins - 1)
                                      : (uint32_t)kRadixBins + lane;
             dig[r] = d;
@@ -209,36 +211,40 @@ __global__ void __launch_bounds__(256) k_hist_u32(SortCtl *__restrict__ ctl,
     }
 }
 
-template <typename KeyT>
-cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, KeyT *ka, uint32_t *va,
-                        KeyT *kb, uint32_t *vb,
-                        bool identity_vals, uint32_t *tile_status, uint32_t max_n,
-                        int max_passes, int grid, cudaStream_t st, uint32_t *status)
+template <typename KeyT, typename ValT>
+cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, void *ka_, void *va_,
+                          void *kb_, void *vb_, bool identity_vals, uint32_t *tile_status,
+                          uint32_t max_n, int max_passes, int grid, cudaStream_t st,
+                          uint32_t *status)
 {
-    const size_t smem = sizeof(SortSmem<KeyT>);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT>,
+    const size_t smem = sizeof(SortSmem<KeyT, ValT>);
+    static int per_sm = 0;  // resident blocks per SM (persistent grid)
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<KeyT, ValT>,
+                                                          kSortThreads, smem);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
+    grid *= per_sm;
     const size_t tstride = sort_status_words(max_n) / 2;
     cudaError_t e = cudaMemsetAsync(tile_status, 0, tstride * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_sort_status", st);
-    KeyT *kin = ka, *kout = kb;
-    uint32_t *vin = va, *vout = vb;
+    KeyT *kin = (KeyT *)ka_, *kout = (KeyT *)kb_;
+    ValT *vin = (ValT *)va_, *vout = (ValT *)vb_;
     for (int p = 0; p < max_passes; ++p) {
-        k_onesweep<KeyT><<<grid, kSortThreads, smem, st>>>(ctl, kin, (p == 0 && identity_vals) ? nullptr : vin,
-                                                          kout, vout, tile_status, tstride, p, status);
+        k_onesweep<KeyT, ValT><<<grid, kSortThreads, smem, st>>>(
+            ctl, kin, (p == 0 && identity_vals) ? nullptr : vin, kout, vout, tile_status, tstride,
+            p, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         FEC_MARK(ws, name, st);
         KeyT *tk = kin;
         kin = kout;
         kout = tk;
-        uint32_t *tv = vin;
+        ValT *tv = vin;
         vin = vout;
         vout = tv;
     }
@@ -247,23 +253,24 @@ cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, Key
 
 }  // namespace
 
-cudaError_t launch_sort_u32(const Workspace &ws, const char *name, SortCtl *ctl, uint32_t *keys_a,
-                            uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b,
-                            bool identity_vals, uint32_t *tile_status, uint32_t max_n,
-                            int max_passes, int grid, cudaStream_t st, uint32_t *status)
+cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, void *keys_a,
+                        void *vals_a, void *keys_b, void *vals_b, bool key64, bool val64,
+                        bool identity_vals, uint32_t *tile_status, uint32_t max_n, int max_passes,
+                        int grid, cudaStream_t st, uint32_t *status)
 {
-    return launch_sort<uint32_t>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                 tile_status, max_n, max_passes, grid, st, status);
-}
-
-cudaError_t launch_sort_u64(const Workspace &ws, const char *name, SortCtl *ctl,
-                            unsigned long long *keys_a, uint32_t *vals_a,
-                            unsigned long long *keys_b, uint32_t *vals_b, bool identity_vals,
-                            uint32_t *tile_status, uint32_t max_n, int max_passes, int grid,
-                            cudaStream_t st, uint32_t *status)
-{
-    return launch_sort<unsigned long long>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                           tile_status, max_n, max_passes, grid, st, status);
+    using u32 = uint32_t;
+    using u64 = unsigned long long;
+    if (!key64 && !val64)
+        return launch_sort_t<u32, u32>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                       tile_status, max_n, max_passes, grid, st, status);
+    if (!key64)
+        return launch_sort_t<u32, u64>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                       tile_status, max_n, max_passes, grid, st, status);
+    if (!val64)
+        return launch_sort_t<u64, u32>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                       tile_status, max_n, max_passes, grid, st, status);
+    return launch_sort_t<u64, u64>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
+                                   tile_status, max_n, max_passes, grid, st, status);
 }
 
 cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st)

@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(kUnionThreads, 3)
     if (lane == 0) {
         atomicAdd(&plan->ctr[CTR_PAIRS], (unsigned long long)n_pairs);
         atomicAdd(&plan->ctr[CTR_BOX_JOINS], (unsigned long long)(n_yes + n_edges));
+        atomicAdd(&plan->ctr[CTR_EDGES], (unsigned long long)n_edges);
         atomicAdd(&plan->ctr[CTR_POINT_TESTS], (unsigned long long)n_und);
         atomicAdd(&plan->ctr[CTR_SAME_ROOT], (unsigned long long)n_same);
         atomicAdd(&plan->ctr[CTR_QUEUED], (unsigned long long)n_queued);
@@ -776,13 +777,14 @@ __global__ void __launch_bounds__(256)
 // a6: labels in input order.
 __global__ void __launch_bounds__(256)
     k_labels(Plan *plan, const uint32_t *__restrict__ idx_a, const uint32_t *__restrict__ idx_b,
-             const uint32_t *__restrict__ sc_of, const uint32_t *__restrict__ parent,
-             const int32_t *__restrict__ crank, int32_t *__restrict__ labels)
+             uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
+             const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
+             int32_t *__restrict__ labels)
 {
     const uint32_t n = plan->sort.n;
     const uint32_t *__restrict__ idx = (plan->sort.npasses & 1u) ? idx_b : idx_a;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const uint32_t i = idx[p];
+        const uint32_t i = idx[(size_t)p * idx_stride];
         if (i < n) labels[i] = crank[parent[sc_of[p]]];
     }
 }
@@ -834,12 +836,14 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, cudaStream_t st)
+cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, bool packed, cudaStream_t st)
 {
     k_rank<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.kept_val_a(), ws.kept_val_b(), ws.crank);
     FEC_MARK(ws, "k_rank", st);
-    k_labels<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.vals_a, ws.vals_b, ws.sc_of, ws.parent,
-                                         ws.crank, labels);
+    // sorted original indices: the 32-bit values, or the low half of the packed payloads
+    k_labels<<<ws.sms * 8, 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
+                                         (const uint32_t *)ws.vals_b, packed ? 2u : 1u, ws.sc_of,
+                                         ws.parent, ws.crank, labels);
     FEC_MARK(ws, "k_labels", st);
     return cudaGetLastError();
 }

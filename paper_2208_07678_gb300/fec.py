@@ -51,7 +51,7 @@ class fec_stats(ctypes.Structure):
                 ("T2", ctypes.c_int64), ("pair_checks", ctypes.c_int64),
                 ("pair_box_joins", ctypes.c_int64), ("pair_point_tests", ctypes.c_int64),
                 ("pair_same_root", ctypes.c_int64), ("point_evals", ctypes.c_int64),
-                ("pairs_queued", ctypes.c_int64)]
+                ("pairs_queued", ctypes.c_int64), ("boundary_edges", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
