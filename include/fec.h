@@ -163,6 +163,36 @@ int fec_trace_read(const fec_ctx *ctx, fec_trace_entry *out, int cap);
 /* Device workspace bytes fec_cluster needs for n points at radius d. */
 int64_t fec_workspace_bytes(int64_t n, float d);
 
+/* Largest cloud fec_cluster_noalloc accepts. */
+#define FEC_NOALLOC_MAX_POINTS ((int64_t)32768)
+
+/* Cluster one cloud without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or any allocator -- code running inside a host application
+ * that owns all device memory through its own pool, real-time loops where an
+ * allocation (and its implicit device synchronisation) is not allowed, or
+ * plug-ins loaded by a framework that forbids allocating outside its
+ * allocator.  It computes exactly what fec_cluster computes, with the same
+ * argument rules, but its workspace is a 16 MiB array that is part of the
+ * library's device image (every GPU that loads the library holds it until
+ * the process exits), so it needs no context and allocates nothing.
+ *   xyz, labels  caller-owned, host or device memory, as for fec_cluster.
+ *   n            at most FEC_NOALLOC_MAX_POINTS; larger n gives
+ *                FEC_ERR_INVALID_ARG.  A cloud longer than 65,536 grid cells
+ *                (of side about d) along its longest axis gives
+ *                FEC_ERR_OUT_OF_RANGE, and one that needs more boundary
+ *                lists than the array holds gives FEC_ERR_OOM.
+ *   cuda_stream  cudaStream_t to run on (NULL = the default stream).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: each call clears what must start at zero, and calls
+ * are serialised inside the library and return only when their GPU work is
+ * done, because calls whose GPU work overlapped would race on the array. */
+fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, int64_t min_size,
+                               int64_t max_size, int32_t *labels, int32_t *num_clusters,
+                               void *cuda_stream);
+
 /* Static string naming a status. */
 const char *fec_status_string(fec_status status);
 

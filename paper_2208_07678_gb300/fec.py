@@ -29,7 +29,8 @@ FEC_OK, FEC_ERR_NOT_READY, FEC_ERR_TIMEOUT = 0, 7, 9
 # Every function the header declares (checked by the CPU tests against include/fec.h).
 EXPORTS = ("fec_create", "fec_destroy", "fec_cluster", "fec_cluster_batch", "fec_serve_submit",
            "fec_serve_poll", "fec_get_stats", "fec_workspace_bytes", "fec_status_string",
-           "fec_trace_enable", "fec_trace_read")
+           "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc")
+FEC_NOALLOC_MAX_POINTS = 32768
 
 
 class FecError(RuntimeError):
@@ -100,6 +101,8 @@ def load(build_if_missing: bool = False):
     lib.fec_trace_enable.restype = ctypes.c_int
     lib.fec_trace_read.argtypes = [vp, ctypes.POINTER(fec_trace_entry), ctypes.c_int]
     lib.fec_trace_read.restype = ctypes.c_int
+    lib.fec_cluster_noalloc.argtypes = [f32p, i64, ctypes.c_float, i64, i64, vp, i32p, vp]
+    lib.fec_cluster_noalloc.restype = ctypes.c_int
     lib.fec_status_string.argtypes = [ctypes.c_int]
     lib.fec_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -131,6 +134,14 @@ def fec_cluster(ctx, xyz_ptr, n, d, min_size, max_size, labels_ptr) -> tuple[int
     k = ctypes.c_int32(-1)
     st = load().fec_cluster(ctx, xyz_ptr, int(n), float(d), int(min_size), int(max_size),
                             labels_ptr, ctypes.byref(k))
+    return st, k.value
+
+
+def fec_cluster_noalloc(xyz_ptr, n, d, min_size, max_size, labels_ptr, cuda_stream=0):
+    """Returns (status, num_clusters); no context, no allocation."""
+    k = ctypes.c_int32(-1)
+    st = load().fec_cluster_noalloc(xyz_ptr, int(n), float(d), int(min_size), int(max_size),
+                                    labels_ptr, ctypes.byref(k), cuda_stream or None)
     return st, k.value
 
 
