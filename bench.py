@@ -246,6 +246,141 @@ def run_reference(args):
     return 0
 
 
+def measure_batch(fec, torch, dev, stream, steps, seed=4):
+    """Batched frames/s on the 256-frame workload: one fec_cluster_batch call
+    per step (graph-captured, autotuned lanes), against the plain path of one
+    fec_cluster call per frame.  Device-resident inputs."""
+    from paper_2208_07678_gb300 import synth
+
+    frames = synth.batch_256(seed=seed)
+    offs = np.zeros(len(frames) + 1, np.int64)
+    offs[1:] = np.cumsum([f.n for f in frames])
+    xyz = torch.from_numpy(np.concatenate([f.xyz for f in frames])).to(dev)
+    lab = torch.empty(int(offs[-1]), dtype=torch.int32, device=dev)
+    d = [f.d for f in frames]
+    mn = [f.min_size for f in frames]
+    mx = [f.max_size for f in frames]
+    with fec.Context(device=dev.index, cuda_stream=stream.cuda_stream) as bctx:
+        for _ in range(3):  # includes the autotuner's first pass
+            bctx.cluster_batch(xyz, offs, d, mn, mx, labels=lab)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            bctx.cluster_batch(xyz, offs, d, mn, mx, labels=lab)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_batch = e0.elapsed_time(e1) / steps
+        batch_lab = lab.clone()
+        # plain path: one call per frame
+        views = [(xyz[3 * int(offs[f]):3 * int(offs[f + 1])] if xyz.dim() == 1 else
+                  xyz[int(offs[f]):int(offs[f + 1])], lab[int(offs[f]):int(offs[f + 1])])
+                 for f in range(len(frames))]
+        for f, (xv, lv) in enumerate(views):
+            bctx.cluster(xv, d[f], mn[f], mx[f], labels=lv)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for f, (xv, lv) in enumerate(views):
+            bctx.cluster(xv, d[f], mn[f], mx[f], labels=lv)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_plain = e0.elapsed_time(e1)
+        same = bool(torch.equal(batch_lab, lab))
+    nf = len(frames)
+    return {"frames": nf, "points": int(offs[-1]), "frames_per_s": nf / (ms_batch * 1e-3),
+            "ms_per_batch": ms_batch, "Mpoints_per_s": offs[-1] / (ms_batch * 1e-3) / 1e6,
+            "plain_frames_per_s": nf / (ms_plain * 1e-3), "plain_ms": ms_plain,
+            "labels_equal_plain": same}
+
+
+def measure_serve(fec, duration=4.0, rate=400.0, pool=40, seed=5, slots_note="4 worker slots"):
+    """Serving: Poisson arrivals of request clouds (10k-2M points) with
+    per-request d and size bounds; latency = completion - arrival.  Beside
+    it, the plain path (one fec_cluster call at a time, FIFO, same arrivals)."""
+    import threading
+
+    from paper_2208_07678_gb300 import synth
+
+    reqs = [synth.serve_request(seed, i) for i in range(pool)]
+    arrivals = synth.poisson_arrivals(seed, rate, duration)
+    rng = np.random.default_rng([seed, 11])
+    pick = rng.integers(0, pool, size=len(arrivals))
+
+    def run_engine():
+        ctx = fec.Context(device=0)
+        lat, outs, tickets = [], {}, {}
+        done = threading.Event()
+        pending = []
+        lock = threading.Lock()
+
+        def collector():
+            while not (done.is_set() and not pending):
+                with lock:
+                    cur = list(pending)
+                for j, t in cur:
+                    st, _ = ctx.poll(t, 0)
+                    if st == fec.FEC_ERR_NOT_READY:
+                        continue
+                    with lock:
+                        pending.remove((j, t))
+                    lat.append(time.perf_counter() - t0 - arrivals[j])
+                time.sleep(0.0002)
+
+        # warm the slots and workspaces once with the largest requests
+        big = sorted(range(pool), key=lambda i: -reqs[i].n)[:4]
+        for i in big:
+            o = np.empty(reqs[i].n, np.int32)
+            t = ctx.submit(reqs[i].xyz, reqs[i].d, reqs[i].min_size, reqs[i].max_size, o)
+            ctx.poll(t, -1)
+        th = threading.Thread(target=collector)
+        t0 = time.perf_counter()
+        th.start()
+        for j, at in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            r = reqs[pick[j]]
+            outs[j] = np.empty(r.n, np.int32)
+            t = ctx.submit(r.xyz, r.d, r.min_size, r.max_size, outs[j])
+            with lock:
+                pending.append((j, t))
+        done.set()
+        th.join()
+        wall = time.perf_counter() - t0
+        ctx.close()
+        return lat, wall
+
+    def run_plain():
+        ctx = fec.Context(device=0)
+        for i in range(pool):
+            ctx.cluster(reqs[i].xyz, reqs[i].d, reqs[i].min_size, reqs[i].max_size)
+        lat = []
+        t0 = time.perf_counter()
+        for j, at in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            r = reqs[pick[j]]
+            ctx.cluster(r.xyz, r.d, r.min_size, r.max_size)
+            lat.append(time.perf_counter() - t0 - at)
+        wall = time.perf_counter() - t0
+        ctx.close()
+        return lat, wall
+
+    def summary(lat, wall):
+        a = np.sort(np.asarray(lat)) * 1e3
+        pts = float(sum(reqs[pick[j]].n for j in range(len(arrivals))))
+        return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "req_per_s": len(a) / wall,
+                "Mpoints_per_s": pts / wall / 1e6}
+
+    eng = summary(*run_engine())
+    plain = summary(*run_plain())
+    return {"requests": int(len(arrivals)), "offered_req_per_s": rate, "duration_s": duration,
+            "distinct_clouds": pool, "engine": eng, "plain_one_call_at_a_time": plain,
+            "note": f"latency = completion - arrival, inputs in host memory, {slots_note}"}
+
+
 def run_ours(args):
     import torch
 
@@ -322,6 +457,11 @@ def run_ours(args):
     breakdown = {t["name"]: round(t["total_ms"] / args.steps, 4) for t in
                  sorted(trace, key=lambda t: -t["total_ms"])}
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra["batch_256"] = measure_batch(fec, torch, dev, stream, max(3, args.steps))
+        extra["serve"] = measure_serve(fec, duration=args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, sn, dt = time_oracle(cloud, args.cpu_points)
@@ -346,6 +486,7 @@ def run_ours(args):
             "union_work": {k: stats[k] for k in ("pair_checks", "pair_box_joins", "pair_point_tests",
                                                  "pair_same_root", "point_evals",
                                                  "pairs_queued", "boundary_edges")},
+            **extra,
             "trace_ms_per_step": {"total": round(step_total_ms, 4), "traced_step_ms": ms_traced,
                                   "by_kernel": breakdown},
         }
@@ -370,6 +511,9 @@ def main(argv=None):
     ap.add_argument("--ref-points", type=int, default=1_000_000,
                     help="oracle sample size per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-frames and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

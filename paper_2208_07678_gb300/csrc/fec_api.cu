@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fec.h"
+#include "fec_batch.h"
 #include "fec_internal.cuh"
 #include "fec_serve.h"
 
@@ -293,6 +294,7 @@ struct fec_ctx {
     fec_stats last{};
     std::mutex mu;
     ServeEngine *serve = nullptr;
+    BatchEngine *batch = nullptr;
     Trace trace;
     bool tracing = false;
 };
@@ -442,23 +444,6 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int6
 size_t ctx_budget(const fec_ctx *ctx) { return ctx->budget; }
 ServeEngine *ctx_serve(fec_ctx *ctx) { return ctx->serve; }
 
-// Frames one after another through the one-cloud pipeline.
-fec_status batch_locked(fec_ctx *ctx, const float *xyz, const int64_t *offsets, int32_t nb,
-                        const float *d, const int64_t *min_size, const int64_t *max_size,
-                        int32_t *labels, int32_t *num_clusters)
-{
-    fec_status worst = FEC_OK;
-    for (int32_t f = 0; f < nb; ++f) {
-        const int64_t n = offsets[f + 1] - offsets[f];
-        num_clusters[f] = 0;
-        if (n == 0) continue;
-        const fec_status s = cluster_locked(ctx, xyz + 3 * offsets[f], n, d[f], min_size[f],
-                                            max_size[f], labels + offsets[f], &num_clusters[f]);
-        if (s != FEC_OK && worst == FEC_OK) worst = s;
-    }
-    return worst;
-}
-
 }  // namespace fec
 
 extern "C" {
@@ -520,6 +505,7 @@ fec_status fec_create(const fec_options *opt, fec_ctx **out)
         return FEC_ERR_OOM;
     }
     ctx->serve = serve_create(ctx, opt ? opt->autotune_cache : nullptr);
+    ctx->batch = batch_create(ctx->device, ctx->ws.sms, opt ? opt->autotune_cache : nullptr);
     *out = ctx;
     return FEC_OK;
 }
@@ -529,6 +515,7 @@ void fec_destroy(fec_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->serve) serve_destroy(ctx->serve);
+    if (ctx->batch) batch_destroy(ctx->batch);
     ctx->trace.destroy();
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
@@ -571,7 +558,16 @@ fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offs
     if (offsets[nb] > 0 && (!xyz || !labels)) return FEC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FEC_ERR_CUDA;
-    return batch_locked(ctx, xyz, offsets, nb, d, min_size, max_size, labels, num_clusters);
+    if (offsets[nb] == 0) {
+        for (int32_t f = 0; f < nb; ++f) num_clusters[f] = 0;
+        return FEC_OK;
+    }
+    const fec_status s = batch_run(ctx->batch, ctx->stream, ctx->budget, xyz, offsets, nb, d,
+                                   min_size, max_size, labels, num_clusters);
+    ctx->last = fec_stats{};
+    ctx->last.n = offsets[nb];
+    ctx->last.workspace_bytes = (int64_t)(ctx->ws.bytes + batch_bytes(ctx->batch));
+    return s;
 }
 
 fec_status fec_trace_enable(fec_ctx *ctx, int enable)

@@ -36,7 +36,8 @@ constexpr size_t kDefaultBudget = (size_t)40 << 30;  // 40 GiB when the context 
 
 struct Request {
     uint64_t ticket = 0;
-    float *xyz = nullptr;   // pinned copy of the input
+    float *xyz = nullptr;   // pinned copy of the input (from the engine's pool)
+    size_t xyz_cap = 0;
     int64_t n = 0;
     float d = 0;
     int64_t min_size = 0, max_size = 0;
@@ -49,8 +50,44 @@ struct Request {
 
 }  // namespace
 
+// Pinned host buffers reused across requests: allocating and freeing pinned
+// memory per request would serialise the device (freeing pinned memory
+// synchronises it).  Buffers come in power-of-two size classes.
+struct PinnedPool {
+    std::vector<std::pair<size_t, void *>> free_list;  // (capacity, pointer)
+    size_t held = 0;
+
+    void *get(size_t bytes, size_t &cap)
+    {
+        size_t c = 4096;
+        while (c < bytes) c <<= 1;
+        for (size_t i = 0; i < free_list.size(); ++i)
+            if (free_list[i].first == c) {
+                void *p = free_list[i].second;
+                free_list.erase(free_list.begin() + i);
+                cap = c;
+                return p;
+            }
+        void *p = nullptr;
+        if (cudaMallocHost(&p, c) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        held += c;
+        cap = c;
+        return p;
+    }
+    void put(void *p, size_t cap) { free_list.emplace_back(cap, p); }
+    void release_all()
+    {
+        for (auto &e : free_list) cudaFreeHost(e.second);
+        free_list.clear();
+    }
+};
+
 struct ServeEngine {
     fec_ctx *owner = nullptr;
+    PinnedPool pool;
     int device = 0;
     size_t budget = 0;
     size_t in_flight = 0;
@@ -118,7 +155,7 @@ void ServeEngine::worker(int slot)
             r->status = s;
             r->k = k;
             r->done = true;
-            cudaFreeHost(r->xyz);
+            if (r->xyz) pool.put(r->xyz, r->xyz_cap);
             r->xyz = nullptr;
         }
         cv_done.notify_all();
@@ -144,10 +181,11 @@ void serve_destroy(ServeEngine *e)
     e->cv_work.notify_all();
     for (auto &t : e->workers) t.join();
     for (auto &kv : e->all) {
-        if (kv.second->xyz) cudaFreeHost(kv.second->xyz);
+        if (kv.second->xyz) e->pool.put(kv.second->xyz, kv.second->xyz_cap);
         delete kv.second;
     }
     for (fec_ctx *c : e->slots) fec_destroy(c);
+    e->pool.release_all();
     delete e;
 }
 
@@ -193,8 +231,11 @@ fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, 
         return FEC_ERR_BUSY;
     }
     if (n > 0) {
-        if (cudaMallocHost(&r->xyz, (size_t)n * 12) != cudaSuccess) {
-            cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            r->xyz = (float *)e->pool.get((size_t)n * 12, r->xyz_cap);
+        }
+        if (!r->xyz) {
             delete r;
             return FEC_ERR_OOM;
         }
