@@ -461,6 +461,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         extra["batch_256"] = measure_batch(fec, torch, dev, stream, max(3, args.steps))
         extra["serve"] = measure_serve(fec, duration=args.serve_seconds)
+        extra["serve_heavy"] = measure_serve(fec, duration=max(1.0, args.serve_seconds / 2),
+                                             rate=2000.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

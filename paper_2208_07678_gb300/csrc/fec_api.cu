@@ -117,6 +117,10 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.col_hi = (uint32_t *)take(4 * ((size_t)1 << cb));
     ws.edges_cap = lists;
     ws.edges = (uint2 *)take(sizeof(uint2) * lists);
+    size_t es = 1024;
+    while (es < n / 8) es <<= 1;
+    ws.edge_set_size = es;
+    ws.edge_set = (unsigned long long *)take(sizeof(unsigned long long) * es);
     ws.nb_first = (uint32_t *)take(4 * 13 * n);
     ws.nb_cnt = (uint8_t *)take(16 * n);
     ws.scratch_words = (size_t)region_grid(ws, n) * kRegionScratch;

@@ -271,6 +271,8 @@ struct Workspace {
     uint32_t col_bits = 0;         // log2 of its capacity
     uint2 *edges = nullptr;        // boundary edges of the neighbour step
     size_t edges_cap = 0;
+    unsigned long long *edge_set = nullptr;  // hash set of joined root pairs (power of two)
+    size_t edge_set_size = 0;
     uint32_t *nb_first = nullptr;  // per cell: first sub-cell of each neighbour cell (13)
     uint8_t *nb_cnt = nullptr;     // per cell: sub-cell count of each neighbour, K in byte 15
     uint32_t *scratch = nullptr;   // per block of the neighbour step: undecided in-region pairs

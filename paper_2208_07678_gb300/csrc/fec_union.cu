@@ -637,16 +637,39 @@ __global__ void __launch_bounds__(kUnionThreads, 3)
     }
 }
 
-// a4: the boundary edges found by k_region, one union per thread (full
-// occupancy hides the latency of the pointer chasing).
+// a4: the boundary edges found by k_region, one union per distinct pair of
+// region-local roots.  After k_region every sub-cell points at its region
+// root, so many boundary edges name the same pair of roots; a hash set keeps
+// the first of each, and only that one joins (the rest would only add load on
+// the giant component's root).  A full probe window falls back to joining.
 __global__ void __launch_bounds__(256)
-    k_edges(Plan *plan, const uint2 *__restrict__ edges, uint32_t ecap, uint32_t *parent)
+    k_edges(Plan *plan, const uint2 *__restrict__ edges, uint32_t ecap, uint32_t *parent,
+            unsigned long long *__restrict__ set, uint32_t set_mask)
 {
     const uint32_t ne = min(plan->edges_n, ecap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
         const uint2 e = edges[i];
         if (e.x == 0xffffffffu) continue;  // unused buffer slot
-        if (!uf_unite(parent, e.x, e.y)) atomicOr(&plan->status, ST_UNION_CAP);
+        uint32_t ra = parent[e.x], rb = parent[e.y];
+        if (ra == rb) continue;
+        if (ra > rb) {
+            const uint32_t t = ra;
+            ra = rb;
+            rb = t;
+        }
+        const unsigned long long key = ((unsigned long long)ra << 32) | rb;
+        uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & set_mask;
+        bool first = true;
+        for (int probe = 0; probe < 32; ++probe) {
+            const unsigned long long old = atomicCAS(set + h, ~0ull, key);
+            if (old == ~0ull) break;          // inserted: this edge is the first
+            if (old == key) {                 // already seen
+                first = false;
+                break;
+            }
+            h = (h + 1) & set_mask;
+        }
+        if (first && !uf_unite(parent, ra, rb)) atomicOr(&plan->status, ST_UNION_CAP);
     }
 }
 
@@ -774,18 +797,47 @@ __global__ void __launch_bounds__(256)
         crank[v[t]] = (int32_t)t;
 }
 
-// a6: labels in input order.
+// a6: the label of every sub-cell (its root's rank, or -1), written over the
+// component-size array, which is not needed after k_kept.
+__global__ void __launch_bounds__(256)
+    k_sclabel(Plan *plan, const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
+              int32_t *__restrict__ sclab)
+{
+    const uint32_t M = plan->M_s;
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x)
+        sclab[a] = crank[parent[a]];
+}
+
+// a6: labels in input order, four sorted positions per thread.
 __global__ void __launch_bounds__(256)
     k_labels(Plan *plan, const uint32_t *__restrict__ idx_a, const uint32_t *__restrict__ idx_b,
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
-             const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
-             int32_t *__restrict__ labels)
+             const int32_t *__restrict__ sclab, int32_t *__restrict__ labels)
 {
     const uint32_t n = plan->sort.n;
     const uint32_t *__restrict__ idx = (plan->sort.npasses & 1u) ? idx_b : idx_a;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t n4 = n / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        uint32_t i[4];
+        if (idx_stride == 2) {
+            const uint4 v0 = reinterpret_cast<const uint4 *>(idx)[2 * q];
+            const uint4 v1 = reinterpret_cast<const uint4 *>(idx)[2 * q + 1];
+            i[0] = v0.x; i[1] = v0.z; i[2] = v1.x; i[3] = v1.z;
+        } else {
+            const uint4 v = reinterpret_cast<const uint4 *>(idx)[q];
+            i[0] = v.x; i[1] = v.y; i[2] = v.z; i[3] = v.w;
+        }
+        const uint4 sc = reinterpret_cast<const uint4 *>(sc_of)[q];
+        const int32_t l0 = sclab[sc.x], l1 = sclab[sc.y], l2 = sclab[sc.z], l3 = sclab[sc.w];
+        if (i[0] < n) labels[i[0]] = l0;
+        if (i[1] < n) labels[i[1]] = l1;
+        if (i[2] < n) labels[i[2]] = l2;
+        if (i[3] < n) labels[i[3]] = l3;
+    }
+    for (uint32_t p = n4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += gridDim.x * blockDim.x) {
         const uint32_t i = idx[(size_t)p * idx_stride];
-        if (i < n) labels[i] = crank[parent[sc_of[p]]];
+        if (i < n) labels[i] = sclab[sc_of[p]];
     }
 }
 
@@ -818,7 +870,11 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
-    k_edges<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent);
+    cudaError_t e = cudaMemsetAsync(ws.edge_set, 0xff, sizeof(unsigned long long) * ws.edge_set_size, st);
+    if (e != cudaSuccess) return e;
+    FEC_MARK(ws, "memset_edge_set", st);
+    k_edges<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
+                                        (uint32_t)(ws.edge_set_size - 1));
     FEC_MARK(ws, "k_edges", st);
     if (!wide)
         k_pairs<false><<<ws.sms * 2, kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
@@ -841,9 +897,12 @@ cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, bool packed, cudaStre
     k_rank<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.kept_val_a(), ws.kept_val_b(), ws.crank);
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
+    int32_t *sclab = (int32_t *)ws.csize;  // component sizes are no longer needed
+    k_sclabel<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab);
+    FEC_MARK(ws, "k_sclabel", st);
     k_labels<<<ws.sms * 8, 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
                                          (const uint32_t *)ws.vals_b, packed ? 2u : 1u, ws.sc_of,
-                                         ws.parent, ws.crank, labels);
+                                         sclab, labels);
     FEC_MARK(ws, "k_labels", st);
     return cudaGetLastError();
 }
