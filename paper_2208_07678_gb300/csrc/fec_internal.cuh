@@ -67,7 +67,18 @@ constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
 constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a block
 constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept per block
-constexpr uint32_t kRegionCellsPerBlock = 1024;
+#ifndef FEC_REGION_CELLS
+#define FEC_REGION_CELLS 1024
+#endif
+#ifndef FEC_REGION_THREADS
+#define FEC_REGION_THREADS 256
+#endif
+#ifndef FEC_REGION_BLOCKS
+#define FEC_REGION_BLOCKS 4
+#endif
+constexpr uint32_t kRegionCellsPerBlock = FEC_REGION_CELLS;
+constexpr int kRegionThreads = FEC_REGION_THREADS;
+constexpr int kRegionBlocksPerSM = FEC_REGION_BLOCKS;
 constexpr uint32_t kWaitCap = 1u << 22;  // spin iterations before a wait gives up
 constexpr uint32_t kUnionCap = 1u << 20; // retries of one union before it gives up
 
@@ -296,7 +307,7 @@ void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
 inline uint32_t region_grid(const Workspace &ws, uint64_t n)
 {
     const uint64_t regions = (n + kRegionCellsPerBlock - 1) / kRegionCellsPerBlock;
-    const uint64_t g = (uint64_t)ws.sms * 3;
+    const uint64_t g = (uint64_t)ws.sms * kRegionBlocksPerSM;
     return (uint32_t)(regions < g ? (regions ? regions : 1) : g);
 }
 

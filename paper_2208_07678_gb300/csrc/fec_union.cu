@@ -22,7 +22,6 @@ namespace fec {
 namespace {
 
 constexpr int kUnionThreads = 256;
-constexpr int kUnionWarps = kUnionThreads / 32;
 
 // Squared distance of an offset, compared against T2.  Narrow form: each
 // |component| is clamped to R+1 (anything above R already fails the test),
@@ -318,6 +317,7 @@ __global__ void __launch_bounds__(256, 4)
 // shared-memory buffers flushed in chunks.
 // ---------------------------------------------------------------------------
 constexpr int kRegionCells = (int)kRegionCellsPerBlock;
+constexpr int kRegionWarps = kRegionThreads / 32;
 constexpr int kRegionSubs = 8 * kRegionCells;
 constexpr int kRegionBuf = 512;
 
@@ -326,11 +326,11 @@ struct RegionSmem {
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
     uint32_t ecount, qcount, next, region, scount, pad[3];
-    uint32_t nbl[kUnionWarps][16];
-    uint32_t pre[kUnionWarps][16];
-    uint8_t kof[kUnionWarps][112];
-    SubBox sbox[kUnionWarps][8];
-    Rec srep[kUnionWarps][8];
+    uint32_t nbl[kRegionWarps][16];
+    uint32_t pre[kRegionWarps][16];
+    uint8_t kof[kRegionWarps][112];
+    SubBox sbox[kRegionWarps][8];
+    Rec srep[kRegionWarps][8];
 };
 
 __device__ __forceinline__ uint32_t s_find(volatile uint32_t *par, uint32_t x)
@@ -393,7 +393,7 @@ __device__ __forceinline__ void buf_append(uint32_t mask, bool mine, uint2 v, ui
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(kUnionThreads, 3)
+__global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     k_region(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
              const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
              const Rec *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kUnionThreads, 3)
         // phase B: the region's undecided pairs still apart, warp witness tests
         {
             const uint32_t nsc = min(S.scount, scap);
-            for (uint32_t base = w * 32; base < nsc; base += kUnionWarps * 32) {
+            for (uint32_t base = w * 32; base < nsc; base += kRegionWarps * 32) {
                 const uint32_t i = base + lane;
                 uint32_t la = 0, lb = 0;
                 bool live = false;
@@ -862,11 +862,11 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     const uint32_t rgrid = region_grid(ws, prm.n);
     const uint32_t scap = kRegionScratch;
     if (!wide)
-        k_region<false><<<rgrid, kUnionThreads, smem, st>>>(
+        k_region<false><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     else
-        k_region<true><<<rgrid, kUnionThreads, smem, st>>>(
+        k_region<true><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
