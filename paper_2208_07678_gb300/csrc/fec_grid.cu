@@ -334,39 +334,54 @@ __global__ void __launch_bounds__(kScanThreads)
         }
         if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
-        if (tid == 0) {
+        if (warp == 0) {
             unsigned long long tot = 0;
-            for (int w = 0; w < kScanThreads / 32; ++w) {
-                const unsigned long long v = s_warp[w];
-                s_warp[w] = tot;
-                tot += v;
+            for (int w = 0; w < kScanThreads / 32; ++w) tot += s_warp[w];
+            __syncwarp();
+            if (lane == 0) {
+                unsigned long long acc = 0;
+                for (int w = 0; w < kScanThreads / 32; ++w) {
+                    const unsigned long long v = s_warp[w];
+                    s_warp[w] = acc;
+                    acc += v;
+                }
+                st_relaxed64(tstat + tile, (tile == 0 ? kIncl : kAgg) | tot);
             }
-            // look-back over preceding tiles
+            // look-back, 32 preceding tiles per step (one per lane)
             unsigned long long prefix = 0;
-            if (tile == 0) {
-                st_relaxed64(tstat, kIncl | tot);
-            } else {
-                st_relaxed64(tstat + tile, kAgg | tot);
+            if (tile > 0) {
                 int64_t p = (int64_t)tile - 1;
                 uint32_t it = 0;
-                while (p >= 0) {
-                    const unsigned long long s = ld_relaxed64(tstat + p);
-                    const unsigned long long f = s & ~kMask;
-                    if (f == 0) {
+                for (;;) {
+                    const int64_t q = p - lane;
+                    unsigned long long sv = q >= 0 ? ld_relaxed64(tstat + q) : kIncl;
+                    // the nearest inclusive entry, and everything before it published
+                    uint32_t incl_m = __ballot_sync(0xffffffffu, (sv & ~kMask) == kIncl);
+                    const int stop = incl_m ? __ffs(incl_m) - 1 : 31;
+                    bool ready = (sv & ~kMask) != 0 || lane > stop;
+                    while (!__all_sync(0xffffffffu, ready)) {
                         if (++it > kWaitCap) {
-                            atomicOr(&plan->status, ST_WAIT_TIMEOUT);
+                            if (lane == 0) atomicOr(&plan->status, ST_WAIT_TIMEOUT);
                             break;
                         }
                         spin_pause(it);
-                        continue;
+                        if (!ready) {
+                            sv = ld_relaxed64(tstat + q);
+                            ready = (sv & ~kMask) != 0;
+                        }
+                        incl_m = __ballot_sync(0xffffffffu, (sv & ~kMask) == kIncl);
                     }
-                    prefix += s & kMask;
-                    if (f == kIncl) break;
-                    --p;
+                    const int stop2 = incl_m ? __ffs(incl_m) - 1 : 31;
+                    unsigned long long part = (lane <= stop2 && q >= 0) ? (sv & kMask) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    prefix += part;
+                    if (incl_m || it > kWaitCap) break;
+                    p -= 32;
                 }
-                st_relaxed64(tstat + tile, kIncl | ((prefix + tot) & kMask));
+                if (lane == 0) st_relaxed64(tstat + tile, kIncl | ((prefix + tot) & kMask));
             }
-            s_prefix = prefix;
+            if (lane == 0) s_prefix = prefix;
         }
         __syncthreads();
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);

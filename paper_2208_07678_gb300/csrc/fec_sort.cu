@@ -22,6 +22,7 @@ static_assert(kSortThreads >= kRadixBins, "the digit loops need one thread per d
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kLookWin = 8;  // preceding tiles read per look-back step
 
 template <typename KeyT, typename ValT>
 struct SortSmem {
@@ -141,22 +142,35 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
         if (tid < kRadixBins) {
             uint32_t prefix = 0;
             if (tile > 0) {
+                // Windowed: the statuses of up to kLookWin preceding tiles are
+                // loaded at once, so a walk over many tiles costs one memory
+                // latency per window instead of one per tile.
                 int64_t p = (int64_t)tile - 1;
                 uint32_t it = 0;
-                while (p >= 0) {
-                    const uint32_t s = ld_relaxed(tstat + (size_t)p * kRadixBins + tid);
-                    const uint32_t f = s & ~kValMask;
-                    if (f == 0) {
-                        if (++it > kWaitCap) {
-                            atomicOr(status, ST_WAIT_TIMEOUT);
-                            break;
+                bool done = false;
+                while (p >= 0 && !done) {
+                    uint32_t win[kLookWin];
+#pragma unroll
+                    for (int j = 0; j < kLookWin; ++j)
+                        win[j] = (p - j >= 0) ? ld_relaxed(tstat + (size_t)(p - j) * kRadixBins + tid)
+                                              : kFlagIncl;
+#pragma unroll
+                    for (int j = 0; j < kLookWin; ++j) {
+                        if (done) break;
+                        uint32_t s = win[j];
+                        while ((s & ~kValMask) == 0) {  // not published yet: wait for it
+                            if (++it > kWaitCap) {
+                                atomicOr(status, ST_WAIT_TIMEOUT);
+                                s = kFlagIncl;
+                                break;
+                            }
+                            spin_pause(it);
+                            s = ld_relaxed(tstat + (size_t)(p - j) * kRadixBins + tid);
                         }
-                        spin_pause(it);
-                        continue;
+                        if (p - j >= 0) prefix += s & kValMask;
+                        if ((s & ~kValMask) == kFlagIncl) done = true;
                     }
-                    prefix += s & kValMask;
-                    if (f == kFlagIncl) break;
-                    --p;
+                    p -= kLookWin;
                 }
                 st_relaxed(tstat + (size_t)tile * kRadixBins + tid,
                            kFlagIncl | ((prefix + S.cnt[tid]) & kValMask));
