@@ -436,17 +436,46 @@ __global__ void __launch_bounds__(kScanThreads)
     }
 }
 
-// a3: per sub-cell box, count and smallest original index; initialise the
-// union-find and component arrays.  Sub-cells above kBigSubcell points are
-// queued for k_subcell_big.
+// The nominal (grid) centre of the sub-cell containing q, as the cell origin
+// org (in quantised coordinates) and twice the centre's offset from it,
+// cen2 = 2*s*h + h - 1 per axis (s = which half of the cell).  A point p of
+// the same sub-cell lies at 2*(p - org) - cen2 from the centre, in units of
+// half a quantum; both terms stay well inside 32 bits.
+__device__ __forceinline__ void subcell_centre(const int32_t q[3], const int32_t lo[3], int32_t S,
+                                               int32_t h, int32_t org[3], int32_t cen2[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const uint32_t rel = (uint32_t)(q[a] - lo[a]);
+        const uint32_t c = rel / (uint32_t)S;
+        const uint32_t off = rel - c * (uint32_t)S;
+        org[a] = (int32_t)((uint32_t)lo[a] + c * (uint32_t)S);
+        cen2[a] = (off >= (uint32_t)h ? 2 * h : 0) + h - 1;
+    }
+}
+
+__device__ __forceinline__ float centre_dist2(const Rec &r, const int32_t org[3],
+                                              const int32_t cen2[3])
+{
+    const float dx = (float)(2 * (r.x - org[0]) - cen2[0]);
+    const float dy = (float)(2 * (r.y - org[1]) - cen2[1]);
+    const float dz = (float)(2 * (r.z - org[2]) - cen2[2]);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// a3: per sub-cell box, count, smallest original index and representative
+// (the point nearest the sub-cell's nominal centre), in one pass over its
+// points; initialise the union-find and component arrays.  Sub-cells above
+// kBigSubcell points are queued for k_subcell_big.
 __global__ void __launch_bounds__(256)
-    k_subcell_stats(Plan *plan, const Rec *__restrict__ rec, const uint32_t *__restrict__ sc_start,
-                    SubBox *__restrict__ box, uint32_t *__restrict__ sminidx,
-                    uint32_t *__restrict__ parent, uint32_t *__restrict__ csize,
-                    uint32_t *__restrict__ cmin, int32_t *__restrict__ crank,
-                    uint32_t *__restrict__ big, Rec *__restrict__ reps)
+    k_subcell_stats(Plan *plan, Params prm, const Rec *__restrict__ rec,
+                    const uint32_t *__restrict__ sc_start, SubBox *__restrict__ box,
+                    uint32_t *__restrict__ sminidx, uint32_t *__restrict__ parent,
+                    uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
+                    int32_t *__restrict__ crank, uint32_t *__restrict__ big, Rec *__restrict__ reps)
 {
     const uint32_t M = plan->M_s;
+    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
         parent[a] = a;
         csize[a] = 0;
@@ -468,113 +497,103 @@ __global__ void __launch_bounds__(256)
         b.lx = b.ly = b.lz = INT32_MAX;
         b.hx = b.hy = b.hz = INT32_MIN;
         uint32_t mi = 0xffffffffu;
+        const Rec r0 = rec[s];
+        int32_t org[3], cen2[3];
+        const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
+        float best = __int_as_float(0x7f800000);
+        Rec rp = r0;
         for (uint32_t p = s; p < e; ++p) {
             const Rec r = rec[p];
             b.lx = min(b.lx, r.x); b.hx = max(b.hx, r.x);
             b.ly = min(b.ly, r.y); b.hy = max(b.hy, r.y);
             b.lz = min(b.lz, r.z); b.hz = max(b.hz, r.z);
             mi = min(mi, r.idx);
-        }
-        b.start = s;
-        b.count = e - s;
-        box[a] = b;
-        sminidx[a] = mi;
-        // representative: the point nearest the box centre (doubled units)
-        const int cx = b.lx + b.hx, cy = b.ly + b.hy, cz = b.lz + b.hz;
-        float best = __int_as_float(0x7f800000);
-        Rec rp = rec[s];
-        for (uint32_t p = s; p < e; ++p) {
-            const Rec r = rec[p];
-            const float dx = (float)(2 * r.x - cx), dy = (float)(2 * r.y - cy), dz = (float)(2 * r.z - cz);
-            const float dd = dx * dx + dy * dy + dz * dz;
+            const float dd = centre_dist2(r, org, cen2);
             if (dd < best) {
                 best = dd;
                 rp = r;
             }
         }
+        b.start = s;
+        b.count = e - s;
+        box[a] = b;
+        sminidx[a] = mi;
         reps[a] = rp;
     }
 }
 
 // a3: the same for the queued large sub-cells, one block per sub-cell.
 __global__ void __launch_bounds__(256)
-    k_subcell_big(Plan *plan, const Rec *__restrict__ rec, const uint32_t *__restrict__ sc_start,
-                  const uint32_t *__restrict__ big, SubBox *__restrict__ box,
-                  uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
+    k_subcell_big(Plan *plan, Params prm, const Rec *__restrict__ rec,
+                  const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
 {
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
-    __shared__ SubBox s_box;
     const uint32_t nb = plan->n_big;
+    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
         const uint32_t a = big[j];
         const uint32_t s = sc_start[a], e = sc_start[a + 1];
-        int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+        const Rec r0 = rec[s];
+        int32_t org[3], cen2[3];
+        const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
+        int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
         uint32_t mi = 0xffffffffu;
-        for (uint32_t p = s + threadIdx.x; p < e; p += blockDim.x) {
-            const Rec r = rec[p];
-            lo[0] = min(lo[0], r.x); hi[0] = max(hi[0], r.x);
-            lo[1] = min(lo[1], r.y); hi[1] = max(hi[1], r.y);
-            lo[2] = min(lo[2], r.z); hi[2] = max(hi[2], r.z);
-            mi = min(mi, r.idx);
-        }
-#pragma unroll
-        for (int a3 = 0; a3 < 3; ++a3) {
-            lo[a3] = warp_min(lo[a3]);
-            hi[a3] = warp_max(hi[a3]);
-        }
-        mi = warp_min(mi);
-        if (l == 0) {
-            for (int a3 = 0; a3 < 3; ++a3) {
-                s_v[a3][w] = lo[a3];
-                s_v[3 + a3][w] = hi[a3];
-            }
-            s_v[6][w] = (int32_t)mi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            SubBox b;
-            int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
-            uint32_t m = 0xffffffffu;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                for (int a3 = 0; a3 < 3; ++a3) {
-                    L[a3] = min(L[a3], s_v[a3][k]);
-                    H[a3] = max(H[a3], s_v[3 + a3][k]);
-                }
-                m = min(m, (uint32_t)s_v[6][k]);
-            }
-            b.lx = L[0]; b.ly = L[1]; b.lz = L[2];
-            b.hx = H[0]; b.hy = H[1]; b.hz = H[2];
-            b.start = s;
-            b.count = e - s;
-            box[a] = b;
-            sminidx[a] = m;
-            s_box = b;
-        }
-        __syncthreads();
-        // representative: the point nearest the box centre
-        const SubBox b = s_box;
-        const int cx = b.lx + b.hx, cy = b.ly + b.hy, cz = b.lz + b.hz;
         unsigned long long bk = ~0ull;
         for (uint32_t p = s + threadIdx.x; p < e; p += blockDim.x) {
             const Rec r = rec[p];
-            const float dx = (float)(2 * r.x - cx), dy = (float)(2 * r.y - cy), dz = (float)(2 * r.z - cz);
+            L[0] = min(L[0], r.x); H[0] = max(H[0], r.x);
+            L[1] = min(L[1], r.y); H[1] = max(H[1], r.y);
+            L[2] = min(L[2], r.z); H[2] = max(H[2], r.z);
+            mi = min(mi, r.idx);
             const unsigned long long k =
-                ((unsigned long long)__float_as_uint(dx * dx + dy * dy + dz * dz) << 32) | (p - s);
+                ((unsigned long long)__float_as_uint(centre_dist2(r, org, cen2)) << 32) | (p - s);
             bk = k < bk ? k : bk;
         }
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+            L[a3] = warp_min(L[a3]);
+            H[a3] = warp_max(H[a3]);
+        }
+        mi = warp_min(mi);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_xor_sync(0xffffffffu, bk, o);
             bk = u < bk ? u : bk;
         }
-        if (l == 0) s_k[w] = bk;
+        if (l == 0) {
+            for (int a3 = 0; a3 < 3; ++a3) {
+                s_v[a3][w] = L[a3];
+                s_v[3 + a3][w] = H[a3];
+            }
+            s_v[6][w] = (int32_t)mi;
+            s_k[w] = bk;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned long long m = s_k[0];
-            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = s_k[k] < m ? s_k[k] : m;
-            reps[a] = rec[s + (uint32_t)m];
+            SubBox b;
+            int32_t LL[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, HH[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+            uint32_t m = 0xffffffffu;
+            unsigned long long kk = ~0ull;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    LL[a3] = min(LL[a3], s_v[a3][k]);
+                    HH[a3] = max(HH[a3], s_v[3 + a3][k]);
+                }
+                m = min(m, (uint32_t)s_v[6][k]);
+                kk = s_k[k] < kk ? s_k[k] : kk;
+            }
+            b.lx = LL[0]; b.ly = LL[1]; b.lz = LL[2];
+            b.hx = HH[0]; b.hy = HH[1]; b.hz = HH[2];
+            b.start = s;
+            b.count = e - s;
+            box[a] = b;
+            sminidx[a] = m;
+            reps[a] = rec[s + (uint32_t)kk];
         }
         __syncthreads();
     }
@@ -674,10 +693,10 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
             ws.scan_status);
     }
     FEC_MARK(ws, "k_cells_u64", st);
-    k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.box, ws.sminidx,
+    k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);
     FEC_MARK(ws, "k_subcell_stats", st);
-    k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.rec, ws.sc_start, ws.big, ws.box,
+    k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
                                               ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_big", st);
     e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);

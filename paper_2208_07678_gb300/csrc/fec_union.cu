@@ -325,7 +325,7 @@ struct RegionSmem {
     uint32_t par[kRegionSubs];
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
-    uint32_t ecount, qcount, next, region, scount, pad[3];
+    uint32_t ecount, qcount, next, region, pad[4];
     uint32_t nbl[kRegionWarps][16];
     uint32_t pre[kRegionWarps][16];
     uint8_t kof[kRegionWarps][112];
@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     // this block's list of undecided in-region pairs (local indices a | b << 16
     // would not fit 8192 sub-cells twice, so two u16 halves of a u32: a, b < 8192)
     uint32_t *const my_scratch = scratch + (size_t)blockIdx.x * scap;
+    const uint32_t wcap = scap / kRegionWarps;  // scratch entries per warp
 
     // Global lists full (more boundary pairs than points): report instead of
     // joining here, which would race with other blocks' phase C.
@@ -441,8 +442,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         }
         __syncthreads();
 
-        if (tid == 0) S.scount = 0;
-        __syncthreads();
+        uint32_t wcount = 0;  // entries this warp put in its scratch slice
         // phase A: decide every pair once
         for (;;) {
             uint32_t c = 0;
@@ -543,12 +543,11 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
                 bool spill = false;
                 if (kmask) {
-                    const int leader = __ffs(kmask) - 1;
-                    uint32_t slot = 0;
-                    if (lane == leader) slot = atomicAdd(&S.scount, (uint32_t)__popc(kmask));
-                    slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(kmask & lanemask_lt());
+                    // this warp's own slice of the block's scratch list
+                    const uint32_t slot = wcount + __popc(kmask & lanemask_lt());
+                    wcount += __popc(kmask);
                     if (keep) {
-                        if (slot < scap) my_scratch[slot] = (a - s0) | ((b - s0) << 16);
+                        if (slot < wcap) my_scratch[w * wcap + slot] = (a - s0) | ((b - s0) << 16);
                         else spill = true;
                     }
                 }
@@ -569,14 +568,15 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         }
         __syncthreads();
         // phase B: the region's undecided pairs still apart, warp witness tests
+        // (each warp takes its own slice, which it filled in phase A)
         {
-            const uint32_t nsc = min(S.scount, scap);
-            for (uint32_t base = w * 32; base < nsc; base += kRegionWarps * 32) {
+            const uint32_t nsc = min(wcount, wcap);
+            for (uint32_t base = 0; base < nsc; base += 32) {
                 const uint32_t i = base + lane;
                 uint32_t la = 0, lb = 0;
                 bool live = false;
                 if (i < nsc) {
-                    const uint32_t v = my_scratch[i];
+                    const uint32_t v = my_scratch[w * wcap + i];
                     la = v & 0xffffu;
                     lb = v >> 16;
                     live = s_find(vpar, la) != s_find(vpar, lb);
