@@ -19,7 +19,7 @@
  * Limits.  0 <= n <= FEC_MAX_POINTS.  |q| < 2^23 on every axis (|x| < 8192 m).
  * d finite and > 0.  0 <= min_size <= max_size (INT64_MAX = unbounded).  The
  * uniform grid with cell side about d over the cloud's bounding box must be
- * addressable with a 61-bit cell key (always true for d >= 0.5 mm over an
+ * addressable with a 61-bit cell key (always true for d >= 1 cm over an
  * 8 km cube); otherwise FEC_ERR_OUT_OF_RANGE.
  *
  * Memory.  Every buffer passed in is owned by the caller.  A context owns its

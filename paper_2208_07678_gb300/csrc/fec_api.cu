@@ -41,6 +41,12 @@ Params make_params(uint32_t n, float d)
     p.S = (int32_t)(2 * h);
     p.slab_cap = (uint32_t)(((1u << 24) - 1) / (uint32_t)p.S + 2);
     p.packed = p.S <= 1024 ? 1u : 0u;
+    // floor(rel / S) for rel < 2^24 as (rel * m) >> s: with s = 24 + ceil(log2 S)
+    // and m = ceil(2^s / S) the product overshoots rel / S by less than 1/S.
+    uint32_t lg = 0;
+    while (((int64_t)1 << lg) < (int64_t)p.S) ++lg;
+    p.div_s = 24 + lg;
+    p.div_m = (uint32_t)((((uint64_t)1 << p.div_s) + (uint64_t)p.S - 1) / (uint64_t)p.S);
     return p;
 }
 

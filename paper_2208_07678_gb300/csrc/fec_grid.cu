@@ -80,11 +80,36 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, uin
     int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
     int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
     uint32_t st = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    // Four consecutive points (48 bytes: three 16-byte loads when aligned)
+    // per thread and step.
+    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
+    const uint32_t ngroups = (n + 3) / 4;
+    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngroups;
+         gi += gridDim.x * blockDim.x) {
+        const uint32_t i0 = gi * 4;
+        const uint32_t cnt = min(4u, n - i0);
+        float f[12];
+        if (vec && cnt == 4) {
+            const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * (size_t)gi;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+            for (int t = 0; t < 3; ++t) {
+                const float4 v = __ldcs(src + t);
+                f[4 * t + 0] = v.x;
+                f[4 * t + 1] = v.y;
+                f[4 * t + 2] = v.z;
+                f[4 * t + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 12; ++t)
+                f[t] = (uint32_t)t < 3 * cnt ? __ldcs(xyz + 3 * (size_t)i0 + t) : 0.0f;
+        }
+#pragma unroll
+        for (int t = 0; t < 12; ++t) {
+            if ((uint32_t)t >= 3 * cnt) break;
+            const int a = t % 3;
             int32_t q;
-            const int e = quantize1(xyz[3 * (size_t)i + a], q);
+            const int e = quantize1(f[t], q);
             if (e == 1) st |= ST_NONFINITE;
             else if (e == 2) st |= ST_OUT_OF_RANGE;
             else {
@@ -167,15 +192,24 @@ __global__ void k_plan(Plan *plan, Params prm)
     plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
 }
 
+// Element i (0..2) of a 3-vector held in registers (no local-memory indexing).
+template <typename T>
+__device__ __forceinline__ T sel3(const T v[3], int i)
+{
+    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
 // Grid coordinates of a quantised point under the plan.
 struct GridMap {
     int32_t lo[3];
     int perm[3];
     uint32_t bits[3];
     int32_t S, h;
+    uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
 
     __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
     {
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             lo[a] = plan->lo[a];
             perm[a] = plan->perm[a];
@@ -183,51 +217,56 @@ struct GridMap {
         }
         S = prm.S;
         h = prm.h;
+        div_m = prm.div_m;
+        div_s = prm.div_s;
+    }
+    // Cell coordinate and offset inside the cell, per original axis.
+    __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t rel = (uint32_t)(q[a] - lo[a]);
+            c[a] = (uint32_t)(((unsigned long long)rel * div_m) >> div_s);
+            off[a] = rel - c[a] * (uint32_t)S;
+        }
     }
     // Sort key: [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2], c = cell coordinate,
     // s = which half of the cell (sub-cell bit).
-    __device__ __forceinline__ unsigned long long key(const int32_t q[3]) const
+    __device__ __forceinline__ unsigned long long key_of(const uint32_t c[3], const uint32_t off[3]) const
     {
         unsigned long long k = 0;
         uint32_t sub = 0;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const uint32_t rel = (uint32_t)(q[perm[p]] - lo[perm[p]]);
-            const uint32_t c = rel / (uint32_t)S;
-            const uint32_t s = (rel - c * (uint32_t)S) >= (uint32_t)h ? 1u : 0u;
-            k = (k << bits[p]) | c;
-            sub = (sub << 1) | s;
+            k = (k << bits[p]) | sel3(c, perm[p]);
+            sub = (sub << 1) | (sel3(off, perm[p]) >= (uint32_t)h ? 1u : 0u);
         }
         return (k << 3) | sub;
     }
     // Sort payload of the packed layout: the original index in the low 32
     // bits and the point's offsets inside its cell (original axes x, y, z,
     // 10 bits each, S <= 1024) above it.
-    __device__ __forceinline__ unsigned long long payload(const int32_t q[3], uint32_t idx) const
+    __device__ __forceinline__ unsigned long long payload_of(const uint32_t off[3], uint32_t idx) const
     {
-        unsigned long long v = idx;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const uint32_t rel = (uint32_t)(q[a] - lo[a]);
-            const uint32_t off = rel - (rel / (uint32_t)S) * (uint32_t)S;
-            v |= (unsigned long long)off << (32 + 10 * a);
-        }
-        return v;
+        return (unsigned long long)idx | ((unsigned long long)off[0] << 32) |
+               ((unsigned long long)off[1] << 42) | ((unsigned long long)off[2] << 52);
     }
-    // Inverse of key() + payload(): the quantised coordinates of a point.
+    // Inverse of key_of() + payload_of(): the quantised coordinates of a point.
     __device__ __forceinline__ void unpack(unsigned long long key, unsigned long long v,
                                            int32_t q[3]) const
     {
         unsigned long long ck = key >> 3;
-        uint32_t c[3];
+        uint32_t cp[3];
 #pragma unroll
         for (int p = 2; p >= 0; --p) {
-            c[perm[p]] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
+            cp[p] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
             ck >>= bits[p];
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            q[a] = lo[a] + (int32_t)(c[a] * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t c = perm[0] == a ? cp[0] : (perm[1] == a ? cp[1] : cp[2]);
+            q[a] = lo[a] + (int32_t)(c * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
+        }
     }
 };
 
@@ -248,14 +287,66 @@ __global__ void __launch_bounds__(256)
     GridMap g;
     g.load(plan, prm);
     __syncthreads();
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int32_t q[3];
+    // Four consecutive points per thread and step: three 16-byte loads of
+    // their coordinates when aligned, vector stores of keys and payloads.
+    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
+    const uint32_t ngroups = (n + 3) / 4;
+    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngroups;
+         gi += gridDim.x * blockDim.x) {
+        const uint32_t i0 = gi * 4;
+        const uint32_t cnt = min(4u, n - i0);
+        float f[12];
+        if (vec && cnt == 4) {
+            const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * (size_t)gi;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) quantize1(xyz[3 * (size_t)i + a], q[a]);
-        const KeyT k = (KeyT)g.key(q);
-        keys[i] = k;
-        if (PACKED) vals[i] = g.payload(q, i);
-        for (int p = 0; p < np; ++p) atomicAdd(&h[p][(uint32_t)(k >> (p * kRadixBits)) & 255u], 1u);
+            for (int t = 0; t < 3; ++t) {
+                const float4 v = __ldcs(src + t);
+                f[4 * t + 0] = v.x;
+                f[4 * t + 1] = v.y;
+                f[4 * t + 2] = v.z;
+                f[4 * t + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 12; ++t)
+                f[t] = (uint32_t)t < 3 * cnt ? __ldcs(xyz + 3 * (size_t)i0 + t) : 0.0f;
+        }
+        KeyT k[4];
+        unsigned long long v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int32_t q[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) quantize1(f[3 * u + a], q[a]);
+            uint32_t c[3], off[3];
+            g.cell_of(q, c, off);
+            k[u] = (KeyT)g.key_of(c, off);
+            v[u] = g.payload_of(off, i0 + u);
+        }
+        if (cnt == 4) {
+            if (sizeof(KeyT) == 4) {
+                reinterpret_cast<uint4 *>(keys)[gi] =
+                    make_uint4((uint32_t)k[0], (uint32_t)k[1], (uint32_t)k[2], (uint32_t)k[3]);
+            } else {
+                reinterpret_cast<ulonglong2 *>(keys)[2 * gi] = make_ulonglong2(k[0], k[1]);
+                reinterpret_cast<ulonglong2 *>(keys)[2 * gi + 1] = make_ulonglong2(k[2], k[3]);
+            }
+            if (PACKED) {
+                reinterpret_cast<ulonglong2 *>(vals)[2 * gi] = make_ulonglong2(v[0], v[1]);
+                reinterpret_cast<ulonglong2 *>(vals)[2 * gi + 1] = make_ulonglong2(v[2], v[3]);
+            }
+        } else {
+            for (uint32_t u = 0; u < cnt; ++u) {
+                keys[i0 + u] = k[u];
+                if (PACKED) vals[i0 + u] = v[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if ((uint32_t)u >= cnt) break;
+            for (int p = 0; p < np; ++p)
+                atomicAdd(&h[p][(uint32_t)(k[u] >> (p * kRadixBits)) & 255u], 1u);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {

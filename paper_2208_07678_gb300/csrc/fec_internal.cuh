@@ -123,6 +123,8 @@ struct Params {
     uint32_t slab_cap;   // entries of the slab index (>= max major cell coordinate + 1)
     uint32_t col_bits;   // log2 of the dense column index capacity
     uint32_t packed;     // 1: sort values carry the in-cell offsets (S <= 1024)
+    // floor(rel / S) == (rel * div_m) >> div_s for every rel < 2^24
+    uint32_t div_m, div_s;
 };
 
 // Quantised point record in cell order: coordinates and the original index.

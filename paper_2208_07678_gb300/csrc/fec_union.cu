@@ -808,7 +808,8 @@ __global__ void __launch_bounds__(256)
         sclab[a] = crank[parent[a]];
 }
 
-// a6: labels in input order, four sorted positions per thread.
+// a6: labels in input order, eight sorted positions per thread and step
+// (all loads of a step issued before their results are used).
 __global__ void __launch_bounds__(256)
     k_labels(Plan *plan, const uint32_t *__restrict__ idx_a, const uint32_t *__restrict__ idx_b,
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
@@ -816,25 +817,44 @@ __global__ void __launch_bounds__(256)
 {
     const uint32_t n = plan->sort.n;
     const uint32_t *__restrict__ idx = (plan->sort.npasses & 1u) ? idx_b : idx_a;
-    const uint32_t n4 = n / 4;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
-        uint32_t i[4];
+    const uint32_t n8 = n / 8;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += gridDim.x * blockDim.x) {
+        uint32_t i[8], sc[8];
         if (idx_stride == 2) {
-            const uint4 v0 = reinterpret_cast<const uint4 *>(idx)[2 * q];
-            const uint4 v1 = reinterpret_cast<const uint4 *>(idx)[2 * q + 1];
-            i[0] = v0.x; i[1] = v0.z; i[2] = v1.x; i[3] = v1.z;
+            const uint4 *src = reinterpret_cast<const uint4 *>(idx) + 4 * (size_t)q;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint4 v = __ldcs(src + t);
+                i[2 * t] = v.x;
+                i[2 * t + 1] = v.z;
+            }
         } else {
-            const uint4 v = reinterpret_cast<const uint4 *>(idx)[q];
-            i[0] = v.x; i[1] = v.y; i[2] = v.z; i[3] = v.w;
+            const uint4 *src = reinterpret_cast<const uint4 *>(idx) + 2 * (size_t)q;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint4 v = __ldcs(src + t);
+                i[4 * t] = v.x;
+                i[4 * t + 1] = v.y;
+                i[4 * t + 2] = v.z;
+                i[4 * t + 3] = v.w;
+            }
         }
-        const uint4 sc = reinterpret_cast<const uint4 *>(sc_of)[q];
-        const int32_t l0 = sclab[sc.x], l1 = sclab[sc.y], l2 = sclab[sc.z], l3 = sclab[sc.w];
-        if (i[0] < n) labels[i[0]] = l0;
-        if (i[1] < n) labels[i[1]] = l1;
-        if (i[2] < n) labels[i[2]] = l2;
-        if (i[3] < n) labels[i[3]] = l3;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(sc_of) + 2 * (size_t)q + t);
+            sc[4 * t] = v.x;
+            sc[4 * t + 1] = v.y;
+            sc[4 * t + 2] = v.z;
+            sc[4 * t + 3] = v.w;
+        }
+        int32_t l[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) l[t] = sclab[sc[t]];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (i[t] < n) labels[i[t]] = l[t];
     }
-    for (uint32_t p = n4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
+    for (uint32_t p = n8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += gridDim.x * blockDim.x) {
         const uint32_t i = idx[(size_t)p * idx_stride];
         if (i < n) labels[i] = sclab[sc_of[p]];
