@@ -100,6 +100,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.rec = (Rec *)take(sizeof(Rec) * n);
     ws.sc_of = (uint32_t *)take(4 * n);
     ws.sc_start = (uint32_t *)take(4 * (n + 2));
+    ws.scode = (uint8_t *)take(n);
     ws.box = (SubBox *)take(sizeof(SubBox) * n);
     ws.sminidx = (uint32_t *)take(4 * n);
     ws.parent = (uint32_t *)take(4 * n);

@@ -360,13 +360,15 @@ __global__ void __launch_bounds__(256)
 // point records (quantised coordinates + original index).
 //   sc_of[p]      sub-cell of sorted position p
 //   sc_start[a]   first sorted position of sub-cell a (sc_start[M_s] = n)
+//   scode[a]      sub-cell code of a: which half of its cell on each axis
 //   cell_key[c]   cell key of cell c; cell_sc[c] first sub-cell of cell c
 template <typename KeyT, typename ValT>
 __global__ void __launch_bounds__(kScanThreads)
     k_cells(Plan *plan, Params prm, const KeyT *__restrict__ keys_a, const ValT *__restrict__ vals_a,
             const KeyT *__restrict__ keys_b, const ValT *__restrict__ vals_b,
             const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
-            uint32_t *__restrict__ sc_start, unsigned long long *__restrict__ cell_key,
+            uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
+            unsigned long long *__restrict__ cell_key,
             uint32_t *__restrict__ cell_sc, unsigned long long *__restrict__ tstat)
 {
     constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
@@ -497,7 +499,10 @@ __global__ void __launch_bounds__(kScanThreads)
                 continue;
             }
             sc_of[p] = sc;
-            if (sh) sc_start[sc] = p;
+            if (sh) {
+                sc_start[sc] = p;
+                scode[sc] = (uint8_t)(k[i] & 7u);
+            }
             if (ch) {
                 cell_key[c] = (unsigned long long)(k[i] >> 3);
                 cell_sc[c] = sc;
@@ -765,22 +770,22 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     if (prm.packed) {
         k_cells<u32, u64><<<grid, kScanThreads, 0, st>>>(
             ws.plan, prm, (const u32 *)ws.keys_a, (const u64 *)ws.vals_a, (const u32 *)ws.keys_b,
-            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
             ws.scan_status);
         FEC_MARK(ws, "k_cells_u32", st);
         k_cells<u64, u64><<<grid, kScanThreads, 0, st>>>(
             ws.plan, prm, (const u64 *)ws.keys_a, (const u64 *)ws.vals_a, (const u64 *)ws.keys_b,
-            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
             ws.scan_status);
     } else {
         k_cells<u32, u32><<<grid, kScanThreads, 0, st>>>(
             ws.plan, prm, (const u32 *)ws.keys_a, (const u32 *)ws.vals_a, (const u32 *)ws.keys_b,
-            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
             ws.scan_status);
         FEC_MARK(ws, "k_cells_u32", st);
         k_cells<u64, u32><<<grid, kScanThreads, 0, st>>>(
             ws.plan, prm, (const u64 *)ws.keys_a, (const u32 *)ws.vals_a, (const u64 *)ws.keys_b,
-            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.cell_key, ws.cell_sc,
+            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
             ws.scan_status);
     }
     FEC_MARK(ws, "k_cells_u64", st);

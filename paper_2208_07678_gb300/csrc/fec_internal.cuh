@@ -266,6 +266,7 @@ struct Workspace {
     Rec *rec = nullptr;
     uint32_t *sc_of = nullptr;
     uint32_t *sc_start = nullptr;  // cap_n + 1
+    uint8_t *scode = nullptr;      // per sub-cell: which half of its cell on each axis
     SubBox *box = nullptr;
     uint32_t *sminidx = nullptr;
     uint32_t *parent = nullptr;

@@ -264,8 +264,13 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
 __constant__ uint32_t kRecip[9] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192};
 
 // a4: half-stencil neighbour lists, one thread per cell: for each of the
-// cell's K <= 13 neighbour cells, its first sub-cell and sub-cell count.
-//   nb_first[c * 13 + k], nb_cnt[c * 16 + k] (k < K), nb_cnt[c * 16 + 15] = K
+// cell's K <= 13 neighbour cells, its first sub-cell, its sub-cell count and
+// its offset from the cell (per permuted axis, in sub-cell-code bit order:
+// bit 2 = p0, bit 1 = p1, bit 0 = p2):
+//   nb_first[c * 13 + k]
+//   nb_cnt[c * 16 + k] = (count - 1) | axes at +1 << 3 | axes at -1 << 6   (k < K)
+//   nb_cnt[c * 16 + 15] = K
+// (p0 is never at -1 in the half stencil, so two bits hold the -1 axes.)
 __global__ void __launch_bounds__(256, 4)
     k_nbrs(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
            const uint32_t *__restrict__ cell_sc, const uint32_t *__restrict__ slab_lo,
@@ -275,6 +280,7 @@ __global__ void __launch_bounds__(256, 4)
 {
     const uint32_t M = plan->M_c;
     const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
+    const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
         const unsigned long long ck = cell_key[c];
         uint32_t cnt[16];
@@ -287,7 +293,13 @@ __global__ void __launch_bounds__(256, 4)
             for (int t = 0; t < nf; ++t) {
                 const uint32_t q = f[t], first = cell_sc[q];
                 nb_first[(size_t)c * 13 + K] = first;
-                cnt[K] = cell_sc[q + 1] - first;
+                const unsigned long long nk = cell_key[q];
+                const long long d0 = (long long)(nk >> (b1 + b2)) - (long long)(ck >> (b1 + b2));
+                const long long d1 = (long long)((nk >> b2) & m1) - (long long)((ck >> b2) & m1);
+                const long long d2 = (long long)(nk & m2) - (long long)(ck & m2);
+                const uint32_t plus = (d0 == 1 ? 4u : 0u) | (d1 == 1 ? 2u : 0u) | (d2 == 1 ? 1u : 0u);
+                const uint32_t minus = (d1 == -1 ? 2u : 0u) | (d2 == -1 ? 1u : 0u);
+                cnt[K] = ((cell_sc[q + 1] - first - 1) & 7u) | (plus << 3) | (minus << 6);
                 ++K;
             }
         }
@@ -326,11 +338,15 @@ struct RegionSmem {
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
     uint32_t ecount, qcount, next, region, pad[4];
-    uint32_t nbl[kRegionWarps][16];
-    uint32_t pre[kRegionWarps][16];
-    uint8_t kof[kRegionWarps][112];
-    SubBox sbox[kRegionWarps][8];
-    Rec srep[kRegionWarps][8];
+    // per cell slot (two per warp, one per half-warp):
+    uint32_t nbl[2 * kRegionWarps][16];    // per neighbour cell: first sub-cell
+    uint32_t pre[2 * kRegionWarps][16];    //   its first ordinal among the neighbour sub-cells
+    uint8_t kof[2 * kRegionWarps][112];    // per neighbour sub-cell: its neighbour cell
+    uint8_t bcode[2 * kRegionWarps][112];  //   its sub-cell code (which half on each axis)
+    uint8_t acode[2 * kRegionWarps][8];    // sub-cell codes of the cell
+    uint8_t nmask[2 * kRegionWarps][16];   // per neighbour cell: axes at +1 (bits 0-2), at -1 (3-4)
+    uint32_t qa[kRegionWarps][64];         // queued pairs (a, b) of each warp
+    uint32_t qb[kRegionWarps][64];
 };
 
 __device__ __forceinline__ uint32_t s_find(volatile uint32_t *par, uint32_t x)
@@ -398,6 +414,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
              const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
              const Rec *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
              const uint32_t *__restrict__ nb_first, const uint8_t *__restrict__ nb_cnt,
+             const uint8_t *__restrict__ scode,
              uint2 *__restrict__ pairq, uint32_t qcap, uint2 *__restrict__ edges, uint32_t ecap,
              uint32_t *__restrict__ scratch, uint32_t scap)
 {
@@ -443,126 +460,173 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         __syncthreads();
 
         uint32_t wcount = 0;  // entries this warp put in its scratch slice
-        // phase A: decide every pair once
+        // phase A: the warp enumerates the pairs of its cells (one cell after
+        // another), drops those that no point pair can join, and queues the
+        // rest in shared memory; every 32 queued pairs are decided together.
+        uint32_t qn = 0;                  // pairs in the warp's queue
+        // Each half-warp (16 lanes) enumerates one cell, so that the two
+        // cells' set-up loads are in flight together.
+        const int hw = lane >> 4, hl = lane & 15;
+        const int cs = 2 * w + hw;        // this half's cell slot in shared memory
+        uint32_t a_lo = 0, na = 0, P0 = 0, P = 0, rcp = 0, next_i = 0, Pmax = 0;
+        bool cells_left = true;
         for (;;) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&S.next, 1u);
-            c = __shfl_sync(0xffffffffu, c, 0);
-            if (c >= c_hi) break;
-            const uint32_t a_lo = cell_sc[c], na = cell_sc[c + 1] - a_lo;
-            if (lane < (int)na) {
-                S.sbox[w][lane] = box[a_lo + lane];
-                S.srep[w][lane] = reps[a_lo + lane];
-            }
-            // neighbour list: counts of up to 13 neighbours (+ K in byte 15)
-            const uint32_t cw = lane < 4 ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 4 + lane] : 0u;
-            const int K = (int)(__shfl_sync(0xffffffffu, cw, 3) >> 24);
-            const uint32_t cword = __shfl_sync(0xffffffffu, cw, (lane >> 2) & 3);
-            const uint32_t cnt = lane < K ? (cword >> (8 * (lane & 3))) & 255u : 0u;
-            const uint32_t first = lane < K ? nb_first[(size_t)c * 13 + lane] : 0u;
-            uint32_t ci = cnt;
+            while (qn < 32 && cells_left) {
+                if (next_i >= Pmax) {  // set up the warp's next two cells
+                    uint32_t c0 = 0;
+                    if (lane == 0) c0 = atomicAdd(&S.next, 2u);
+                    c0 = __shfl_sync(0xffffffffu, c0, 0);
+                    if (c0 >= c_hi) {
+                        cells_left = false;
+                        break;
+                    }
+                    const uint32_t c = c0 + hw;
+                    const bool have = c < c_hi;
+                    a_lo = have ? cell_sc[c] : 0u;
+                    na = have ? cell_sc[c + 1] - a_lo : 0u;
+                    // neighbour list: per neighbour one byte (count - 1,
+                    // offset masks), K in byte 15
+                    const uint32_t cw = (have && hl < 4) ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 4 + hl] : 0u;
+                    const int K = (int)(__shfl_sync(0xffffffffu, cw, 3, 16) >> 24);
+                    const uint32_t cword = __shfl_sync(0xffffffffu, cw, (hl >> 2) & 3, 16);
+                    const uint32_t nbyte = (cword >> (8 * (hl & 3))) & 255u;
+                    const uint32_t cnt = hl < K ? (nbyte & 7u) + 1u : 0u;
+                    const uint32_t first = hl < K ? nb_first[(size_t)c * 13 + hl] : 0u;
+                    if (hl < (int)na) S.acode[cs][hl] = scode[a_lo + hl];
+                    uint32_t ci = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, ci, o);
-                if (lane >= o) ci += u;
-            }
-            const uint32_t T = __shfl_sync(0xffffffffu, ci, 31);
-            if (lane < K) {
-                S.nbl[w][lane] = first;
-                S.pre[w][lane] = ci - cnt;
-                for (uint32_t j = ci - cnt; j < ci; ++j) S.kof[w][j] = (uint8_t)lane;
-            }
-            __syncwarp();
-            const uint32_t P0 = na * (na - 1) / 2;
-            const uint32_t P = P0 + na * T;
-            const uint32_t rcp = kRecip[na];
-
-            for (uint32_t base = 0; base < P; base += 32) {
-                const uint32_t i = base + lane;
-                int dec = 0;
-                bool local = true;
-                uint32_t ia = 0, a = 0, b = 0;
+                    for (int o = 1; o < 16; o <<= 1) {
+                        const uint32_t u = __shfl_up_sync(0xffffffffu, ci, o, 16);
+                        if (hl >= o) ci += u;
+                    }
+                    const uint32_t T = __shfl_sync(0xffffffffu, ci, 15, 16);
+                    if (hl < K) {
+                        S.nbl[cs][hl] = first;
+                        S.pre[cs][hl] = ci - cnt;
+                        S.nmask[cs][hl] = (uint8_t)(nbyte >> 3);
+                        for (uint32_t j = ci - cnt; j < ci; ++j) S.kof[cs][j] = (uint8_t)hl;
+                    }
+                    __syncwarp();
+                    for (uint32_t j = hl; j < T; j += 16) {
+                        const uint32_t k = S.kof[cs][j];
+                        S.bcode[cs][j] = scode[S.nbl[cs][k] + (j - S.pre[cs][k])];
+                    }
+                    __syncwarp();
+                    P0 = na * (na - 1) / 2;
+                    P = P0 + na * T;
+                    rcp = kRecip[na];
+                    next_i = 0;
+                    Pmax = max(P, __shfl_xor_sync(0xffffffffu, P, 16));
+                    continue;
+                }
+                const uint32_t i = next_i + hl;
+                next_i += 16;
+                bool possible = false;
+                uint32_t a = 0, b = 0;
                 if (i < P) {
-                    SubBox BB;
-                    Rec RB;
                     if (i < P0) {
-                        uint32_t rem = i, ib;
-                        ia = 0;
+                        uint32_t rem = i, ia = 0;
                         while (rem >= na - 1 - ia) {
                             rem -= na - 1 - ia;
                             ++ia;
                         }
-                        ib = ia + 1 + rem;
-                        b = a_lo + ib;
                         a = a_lo + ia;
-                        if (s_find(vpar, a - s0) != s_find(vpar, b - s0)) {
-                            BB = S.sbox[w][ib];
-                            RB = S.srep[w][ib];
-                            dec = 3;  // decide below
-                        } else {
-                            ++n_same;
-                        }
+                        b = a_lo + ia + 1 + rem;
+                        possible = true;
                     } else {
                         const uint32_t j = i - P0;
                         const uint32_t jb = (j * rcp) >> 16;
-                        ia = j - jb * na;
-                        const uint32_t k = S.kof[w][jb];
-                        b = S.nbl[w][k] + (jb - S.pre[w][k]);
+                        const uint32_t ia = j - jb * na;
+                        const uint32_t k = S.kof[cs][jb];
+                        b = S.nbl[cs][k] + (jb - S.pre[cs][k]);
                         a = a_lo + ia;
-                        local = b >= s0 && b < s1;
-                        if (!local || s_find(vpar, a - s0) != s_find(vpar, b - s0)) {
-                            BB = box[b];
-                            RB = reps[b];
-                            dec = 3;
-                        } else {
-                            ++n_same;
-                        }
-                    }
-                    if (dec == 3) {
-                        ++n_pairs;
-                        dec = box_decide<WIDE>(S.sbox[w][ia], BB, S.srep[w][ia], RB, m);
+                        // Sub-cells three sub-cell steps apart on an axis are
+                        // more than 2h >= R apart: along an axis where the
+                        // neighbour cell is at +1, a in the lower half and b
+                        // in the upper half (at -1: the reverse) cannot join.
+                        const uint32_t A = S.acode[cs][ia], B = S.bcode[cs][jb];
+                        const uint32_t nm = S.nmask[cs][k];
+                        possible = (((nm & 7u) & ~A & B) | ((nm >> 3) & A & ~B)) == 0;
                     }
                 }
-                if (dec == 1 && local) {
-                    ++n_yes;
-                    s_unite(S.par, a - s0, b - s0);
+                const uint32_t pm = __ballot_sync(0xffffffffu, possible);
+                if (possible) {
+                    const uint32_t slot = qn + __popc(pm & lanemask_lt());
+                    S.qa[w][slot] = a;
+                    S.qb[w][slot] = b;
                 }
-                const bool emit = dec == 1 && !local;
-                n_edges += emit ? 1 : 0;
-                buf_append(__ballot_sync(0xffffffffu, emit), emit, make_uint2(a, b), S.ebuf,
-                           &S.ecount, edges, &plan->edges_n, ecap, edge_overflow);
-                const bool und = dec == 2;
-                n_und += und ? 1 : 0;
-                const bool cross = und && !local;
-                n_queued += cross ? 1 : 0;
-                buf_append(__ballot_sync(0xffffffffu, cross), cross, make_uint2(a, b), S.qbuf,
-                           &S.qcount, pairq, &plan->pairq_n, qcap, pair_overflow);
-                // undecided pairs inside the region: the block's scratch list
-                // (or, when it is full, the global queue)
-                const bool keep = und && local;
-                const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
-                bool spill = false;
-                if (kmask) {
-                    // this warp's own slice of the block's scratch list
-                    const uint32_t slot = wcount + __popc(kmask & lanemask_lt());
-                    wcount += __popc(kmask);
-                    if (keep) {
-                        if (slot < wcap) my_scratch[w * wcap + slot] = (a - s0) | ((b - s0) << 16);
-                        else spill = true;
-                    }
+                qn += __popc(pm);
+            }
+            if (qn == 0) break;
+            __syncwarp();
+            // decide the first min(qn, 32) queued pairs, one per lane
+            const uint32_t mq = qn < 32 ? qn : 32;
+            uint32_t a = 0, b = 0;
+            int dec = 0;
+            bool local = true;
+            if ((uint32_t)lane < mq) {
+                a = S.qa[w][lane];
+                b = S.qb[w][lane];
+                local = b - s0 < ns;
+                if (local && s_find(vpar, a - s0) == s_find(vpar, b - s0)) {
+                    ++n_same;
+                } else {
+                    ++n_pairs;
+                    dec = box_decide<WIDE>(box[a], box[b], reps[a], reps[b], m);
                 }
-                // scratch full: test those pairs right here
-                uint32_t smask = __ballot_sync(0xffffffffu, spill);
-                while (smask) {
-                    const int src = __ffs(smask) - 1;
-                    smask &= smask - 1;
-                    const uint32_t pa = __shfl_sync(0xffffffffu, a, src) - s0;
-                    const uint32_t pb = __shfl_sync(0xffffffffu, b, src) - s0;
-                    if (s_find(vpar, pa) == s_find(vpar, pb)) continue;  // warp-uniform
-                    if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
-                        s_unite(S.par, pa, pb);
-                    __syncwarp();
+            }
+            // the rest of the queue (fewer than 32) moves to its front
+            uint32_t ra = 0, rb = 0;
+            const bool rest = (uint32_t)lane + 32 < qn;
+            if (rest) {
+                ra = S.qa[w][lane + 32];
+                rb = S.qb[w][lane + 32];
+            }
+            __syncwarp();
+            if (rest) {
+                S.qa[w][lane] = ra;
+                S.qb[w][lane] = rb;
+            }
+            qn -= mq;
+            if (dec == 1 && local) {
+                ++n_yes;
+                s_unite(S.par, a - s0, b - s0);
+            }
+            const bool emit = dec == 1 && !local;
+            n_edges += emit ? 1 : 0;
+            buf_append(__ballot_sync(0xffffffffu, emit), emit, make_uint2(a, b), S.ebuf,
+                       &S.ecount, edges, &plan->edges_n, ecap, edge_overflow);
+            const bool und = dec == 2;
+            n_und += und ? 1 : 0;
+            const bool cross = und && !local;
+            n_queued += cross ? 1 : 0;
+            buf_append(__ballot_sync(0xffffffffu, cross), cross, make_uint2(a, b), S.qbuf,
+                       &S.qcount, pairq, &plan->pairq_n, qcap, pair_overflow);
+            // undecided pairs inside the region: the block's scratch list
+            // (or, when it is full, the global queue)
+            const bool keep = und && local;
+            const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
+            bool spill = false;
+            if (kmask) {
+                // this warp's own slice of the block's scratch list
+                const uint32_t slot = wcount + __popc(kmask & lanemask_lt());
+                wcount += __popc(kmask);
+                if (keep) {
+                    if (slot < wcap) my_scratch[w * wcap + slot] = (a - s0) | ((b - s0) << 16);
+                    else spill = true;
                 }
+            }
+            // scratch full: test those pairs right here
+            uint32_t smask = __ballot_sync(0xffffffffu, spill);
+            while (smask) {
+                const int src = __ffs(smask) - 1;
+                smask &= smask - 1;
+                const uint32_t pa = __shfl_sync(0xffffffffu, a, src) - s0;
+                const uint32_t pb = __shfl_sync(0xffffffffu, b, src) - s0;
+                if (s_find(vpar, pa) == s_find(vpar, pb)) continue;  // warp-uniform
+                if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
+                    s_unite(S.par, pa, pb);
+                __syncwarp();
             }
             __syncwarp();
         }
@@ -884,11 +948,11 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     if (!wide)
         k_region<false><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
-            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
+            ws.nb_cnt, ws.scode, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     else
         k_region<true><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
-            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
+            ws.nb_cnt, ws.scode, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
     cudaError_t e = cudaMemsetAsync(ws.edge_set, 0xff, sizeof(unsigned long long) * ws.edge_set_size, st);
     if (e != cudaSuccess) return e;
