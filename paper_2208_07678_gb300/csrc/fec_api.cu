@@ -101,6 +101,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.sc_of = (uint32_t *)take(4 * n);
     ws.sc_start = (uint32_t *)take(4 * (n + 2));
     ws.scode = (uint8_t *)take(n);
+    ws.cocc = (uint8_t *)take(n);
     ws.box = (SubBox *)take(sizeof(SubBox) * n);
     ws.sminidx = (uint32_t *)take(4 * n);
     ws.parent = (uint32_t *)take(4 * n);
@@ -129,7 +130,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.edge_set_size = es;
     ws.edge_set = (unsigned long long *)take(sizeof(unsigned long long) * es);
     ws.nb_first = (uint32_t *)take(4 * 13 * n);
-    ws.nb_cnt = (uint8_t *)take(16 * n);
+    ws.nb_cnt = (uint8_t *)take(32 * n);
     ws.scratch_words = (size_t)region_grid(ws, n) * kRegionScratch;
     ws.scratch = (uint32_t *)take(4 * ws.scratch_words);
     off = (off + 255) & ~(size_t)255;

@@ -712,8 +712,10 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(256)
     k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
+            const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
             uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
-            uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi)
+            uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
+            uint8_t *__restrict__ cocc)
 {
     const uint32_t M = plan->M_c;
     const uint32_t b2 = plan->bits[2];
@@ -730,6 +732,12 @@ __global__ void __launch_bounds__(256)
             if (c == 0 || (kp >> b2) != col) col_lo[col] = c;
             if (c + 1 == M || (kn >> b2) != col) col_hi[col] = c + 1;
         }
+        // occupancy of the cell: bit s set when sub-cell code s is present
+        // (its sub-cells are stored in increasing code order)
+        uint32_t occ = 0;
+        const uint32_t e = min(cell_sc[c + 1], cell_sc[c] + 8u);
+        for (uint32_t a = cell_sc[c]; a < e; ++a) occ |= 1u << (scode[a] & 7u);
+        cocc[c] = (uint8_t)occ;
     }
 }
 
@@ -802,7 +810,8 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     FEC_MARK(ws, "memset_slabs", st);
     k_clear_cols<<<grid, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
     FEC_MARK(ws, "k_clear_cols", st);
-    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.slab_lo, ws.slab_hi, ws.col_lo, ws.col_hi);
+    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
+                                  ws.col_lo, ws.col_hi, ws.cocc);
     FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();
 }

@@ -267,6 +267,7 @@ struct Workspace {
     uint32_t *sc_of = nullptr;
     uint32_t *sc_start = nullptr;  // cap_n + 1
     uint8_t *scode = nullptr;      // per sub-cell: which half of its cell on each axis
+    uint8_t *cocc = nullptr;       // per cell: bit s set when its sub-cell with code s exists
     SubBox *box = nullptr;
     uint32_t *sminidx = nullptr;
     uint32_t *parent = nullptr;
@@ -288,7 +289,7 @@ struct Workspace {
     unsigned long long *edge_set = nullptr;  // hash set of joined root pairs (power of two)
     size_t edge_set_size = 0;
     uint32_t *nb_first = nullptr;  // per cell: first sub-cell of each neighbour cell (13)
-    uint8_t *nb_cnt = nullptr;     // per cell: sub-cell count of each neighbour, K in byte 15
+    uint8_t *nb_cnt = nullptr;     // per cell, 32 bytes: neighbour occupancies and offsets
     uint32_t *scratch = nullptr;   // per block of the neighbour step: undecided in-region pairs
     size_t scratch_words = 0;
     uint32_t list_scale = 1;       // boundary-edge and pair lists hold list_scale * 2 * cap_n

@@ -260,30 +260,52 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
                         col_lo, col_hi, f);
 }
 
+// Position of the r-th (from 0) set bit of the 8-bit mask m (r < popc(m)).
+__device__ __forceinline__ uint32_t select8(uint32_t m, uint32_t r)
+{
+    uint32_t pos = 0;
+    const uint32_t c4 = __popc(m & 15u);
+    if (r >= c4) {
+        r -= c4;
+        pos = 4;
+    }
+    const uint32_t c2 = __popc((m >> pos) & 3u);
+    if (r >= c2) {
+        r -= c2;
+        pos += 2;
+    }
+    if (r >= ((m >> pos) & 1u)) pos += 1;
+    return pos;
+}
+
 // ceil(65536 / n) for n = 1..8: i / n == (i * kRecip[n]) >> 16 for i < 8192.
 __constant__ uint32_t kRecip[9] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192};
 
 // a4: half-stencil neighbour lists, one thread per cell: for each of the
-// cell's K <= 13 neighbour cells, its first sub-cell, its sub-cell count and
-// its offset from the cell (per permuted axis, in sub-cell-code bit order:
-// bit 2 = p0, bit 1 = p1, bit 0 = p2):
+// cell's K <= 13 neighbour cells, its first sub-cell, its sub-cell occupancy
+// (bit s set when its sub-cell with code s exists; sub-cells are stored in
+// code order, so the r-th sub-cell has the r-th set bit's code) and its
+// offset from the cell (per permuted axis, in sub-cell-code bit order:
+// bit 2 = p0, bit 1 = p1, bit 0 = p2).  32 bytes per cell:
 //   nb_first[c * 13 + k]
-//   nb_cnt[c * 16 + k] = (count - 1) | axes at +1 << 3 | axes at -1 << 6   (k < K)
-//   nb_cnt[c * 16 + 15] = K
+//   nb[c * 32 + k]      occupancy of neighbour k              (k < K)
+//   nb[c * 32 + 13]     occupancy of the cell itself
+//   nb[c * 32 + 15]     K
+//   nb[c * 32 + 16 + k] axes at +1 | axes at -1 << 3          (k < K)
 // (p0 is never at -1 in the half stencil, so two bits hold the -1 axes.)
 __global__ void __launch_bounds__(256, 4)
     k_nbrs(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
            const uint32_t *__restrict__ cell_sc, const uint32_t *__restrict__ slab_lo,
            const uint32_t *__restrict__ slab_hi, const uint32_t *__restrict__ col_lo,
-           const uint32_t *__restrict__ col_hi, uint32_t *__restrict__ nb_first,
-           uint8_t *__restrict__ nb_cnt)
+           const uint32_t *__restrict__ col_hi, const uint8_t *__restrict__ cocc,
+           uint32_t *__restrict__ nb_first, uint8_t *__restrict__ nb_cnt)
 {
     const uint32_t M = plan->M_c;
     const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
     const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
         const unsigned long long ck = cell_key[c];
-        uint32_t cnt[16];
+        uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int K = 0;
 #pragma unroll
         for (int col = 0; col < 5; ++col) {
@@ -299,14 +321,20 @@ __global__ void __launch_bounds__(256, 4)
                 const long long d2 = (long long)(nk & m2) - (long long)(ck & m2);
                 const uint32_t plus = (d0 == 1 ? 4u : 0u) | (d1 == 1 ? 2u : 0u) | (d2 == 1 ? 1u : 0u);
                 const uint32_t minus = (d1 == -1 ? 2u : 0u) | (d2 == -1 ? 1u : 0u);
-                cnt[K] = ((cell_sc[q + 1] - first - 1) & 7u) | (plus << 3) | (minus << 6);
+                // K < 13, so the word indices below stay in range (unrolled: registers)
+#pragma unroll
+                for (int wi = 0; wi < 4; ++wi) {
+                    if ((K >> 2) == wi) {
+                        wv[wi] |= (uint32_t)cocc[q] << (8 * (K & 3));
+                        wv[4 + wi] |= (plus | (minus << 3)) << (8 * (K & 3));
+                    }
+                }
                 ++K;
             }
         }
-        uint32_t wv[4] = {0, 0, 0, 0};
-        for (int k = 0; k < K; ++k) wv[k >> 2] |= cnt[k] << (8 * (k & 3));
-        wv[3] |= (uint32_t)K << 24;
-        reinterpret_cast<uint4 *>(nb_cnt)[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        wv[3] |= ((uint32_t)cocc[c] << 8) | ((uint32_t)K << 24);
+        reinterpret_cast<uint4 *>(nb_cnt)[2 * (size_t)c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        reinterpret_cast<uint4 *>(nb_cnt)[2 * (size_t)c + 1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
     }
 }
 
@@ -342,8 +370,7 @@ struct RegionSmem {
     uint32_t nbl[2 * kRegionWarps][16];    // per neighbour cell: first sub-cell
     uint32_t pre[2 * kRegionWarps][16];    //   its first ordinal among the neighbour sub-cells
     uint8_t kof[2 * kRegionWarps][112];    // per neighbour sub-cell: its neighbour cell
-    uint8_t bcode[2 * kRegionWarps][112];  //   its sub-cell code (which half on each axis)
-    uint8_t acode[2 * kRegionWarps][8];    // sub-cell codes of the cell
+    uint8_t nocc[2 * kRegionWarps][16];    // per neighbour cell: sub-cell occupancy
     uint8_t nmask[2 * kRegionWarps][16];   // per neighbour cell: axes at +1 (bits 0-2), at -1 (3-4)
     uint32_t qa[kRegionWarps][64];         // queued pairs (a, b) of each warp
     uint32_t qb[kRegionWarps][64];
@@ -414,7 +441,6 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
              const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
              const Rec *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
              const uint32_t *__restrict__ nb_first, const uint8_t *__restrict__ nb_cnt,
-             const uint8_t *__restrict__ scode,
              uint2 *__restrict__ pairq, uint32_t qcap, uint2 *__restrict__ edges, uint32_t ecap,
              uint32_t *__restrict__ scratch, uint32_t scap)
 {
@@ -468,7 +494,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         // cells' set-up loads are in flight together.
         const int hw = lane >> 4, hl = lane & 15;
         const int cs = 2 * w + hw;        // this half's cell slot in shared memory
-        uint32_t a_lo = 0, na = 0, P0 = 0, P = 0, rcp = 0, next_i = 0, Pmax = 0;
+        uint32_t a_lo = 0, na = 0, own = 0, P0 = 0, P = 0, rcp = 0, next_i = 0, Pmax = 0;
         bool cells_left = true;
         for (;;) {
             while (qn < 32 && cells_left) {
@@ -483,16 +509,17 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     const uint32_t c = c0 + hw;
                     const bool have = c < c_hi;
                     a_lo = have ? cell_sc[c] : 0u;
-                    na = have ? cell_sc[c + 1] - a_lo : 0u;
-                    // neighbour list: per neighbour one byte (count - 1,
-                    // offset masks), K in byte 15
-                    const uint32_t cw = (have && hl < 4) ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 4 + hl] : 0u;
-                    const int K = (int)(__shfl_sync(0xffffffffu, cw, 3, 16) >> 24);
-                    const uint32_t cword = __shfl_sync(0xffffffffu, cw, (hl >> 2) & 3, 16);
-                    const uint32_t nbyte = (cword >> (8 * (hl & 3))) & 255u;
-                    const uint32_t cnt = hl < K ? (nbyte & 7u) + 1u : 0u;
+                    // neighbour record (32 bytes): occupancies, offsets, K
+                    const uint32_t cw = (have && hl < 8) ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 8 + hl] : 0u;
+                    const uint32_t w3 = __shfl_sync(0xffffffffu, cw, 3, 16);
+                    const int K = (int)(w3 >> 24);
+                    own = (w3 >> 8) & 255u;
+                    na = __popc(own);
+                    const uint32_t ow = __shfl_sync(0xffffffffu, cw, (hl >> 2) & 3, 16);
+                    const uint32_t mw = __shfl_sync(0xffffffffu, cw, 4 + ((hl >> 2) & 3), 16);
+                    const uint32_t occ = (ow >> (8 * (hl & 3))) & 255u;
+                    const uint32_t cnt = hl < K ? (uint32_t)__popc(occ) : 0u;
                     const uint32_t first = hl < K ? nb_first[(size_t)c * 13 + hl] : 0u;
-                    if (hl < (int)na) S.acode[cs][hl] = scode[a_lo + hl];
                     uint32_t ci = cnt;
 #pragma unroll
                     for (int o = 1; o < 16; o <<= 1) {
@@ -503,13 +530,9 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     if (hl < K) {
                         S.nbl[cs][hl] = first;
                         S.pre[cs][hl] = ci - cnt;
-                        S.nmask[cs][hl] = (uint8_t)(nbyte >> 3);
+                        S.nocc[cs][hl] = (uint8_t)occ;
+                        S.nmask[cs][hl] = (uint8_t)((mw >> (8 * (hl & 3))) & 255u);
                         for (uint32_t j = ci - cnt; j < ci; ++j) S.kof[cs][j] = (uint8_t)hl;
-                    }
-                    __syncwarp();
-                    for (uint32_t j = hl; j < T; j += 16) {
-                        const uint32_t k = S.kof[cs][j];
-                        S.bcode[cs][j] = scode[S.nbl[cs][k] + (j - S.pre[cs][k])];
                     }
                     __syncwarp();
                     P0 = na * (na - 1) / 2;
@@ -544,7 +567,8 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                         // more than 2h >= R apart: along an axis where the
                         // neighbour cell is at +1, a in the lower half and b
                         // in the upper half (at -1: the reverse) cannot join.
-                        const uint32_t A = S.acode[cs][ia], B = S.bcode[cs][jb];
+                        const uint32_t A = select8(own, ia);
+                        const uint32_t B = select8(S.nocc[cs][k], jb - S.pre[cs][k]);
                         const uint32_t nm = S.nmask[cs][k];
                         possible = (((nm & 7u) & ~A & B) | ((nm >> 3) & A & ~B)) == 0;
                     }
@@ -941,18 +965,18 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
         attr = true;
     }
     k_nbrs<<<ws.sms * 8, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
-                                        ws.col_lo, ws.col_hi, ws.nb_first, ws.nb_cnt);
+                                        ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
     const uint32_t scap = kRegionScratch;
     if (!wide)
         k_region<false><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
-            ws.nb_cnt, ws.scode, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
+            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     else
         k_region<true><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
-            ws.nb_cnt, ws.scode, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
+            ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
     cudaError_t e = cudaMemsetAsync(ws.edge_set, 0xff, sizeof(unsigned long long) * ws.edge_set_size, st);
     if (e != cudaSuccess) return e;
