@@ -806,16 +806,30 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
 
 // a5: every sub-cell points at its root; component sizes and smallest
 // original index, aggregated per warp before the atomics.
-__global__ void __launch_bounds__(256)
+constexpr int kFlatSlots = 512;  // per-block table of component sums
+
+__global__ void __launch_bounds__(256, 4)
     k_flatten_stats(Plan *plan, const SubBox *__restrict__ box, const uint32_t *__restrict__ sminidx,
                     uint32_t *parent, uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin)
 {
+    // Each block takes one contiguous range of sub-cells (a compact piece of
+    // space, so few distinct components) and sums sizes and smallest indices
+    // per root in a shared-memory table; roots that find no free slot go
+    // straight to the global arrays.
+    __shared__ uint32_t t_root[kFlatSlots], t_size[kFlatSlots], t_min[kFlatSlots];
+    for (int i = threadIdx.x; i < kFlatSlots; i += blockDim.x) {
+        t_root[i] = 0xffffffffu;
+        t_size[i] = 0;
+        t_min[i] = 0xffffffffu;
+    }
+    __syncthreads();
     const uint32_t M = plan->M_s;
     const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < M; base += stride) {
+    const uint32_t per = (M + gridDim.x - 1) / gridDim.x;
+    const uint32_t lo = blockIdx.x * per, hi = min(M, lo + per);
+    for (uint32_t base = lo + (threadIdx.x & ~31u); base < hi; base += blockDim.x) {
         const uint32_t a = base + lane;
-        const bool valid = a < M;
+        const bool valid = a < hi;
         uint32_t r = 0xffffffffu, cnt = 0, mi = 0xffffffffu;
         if (valid) {
             // read-only walk: unions are finished, pointers only get shorter
@@ -827,21 +841,42 @@ __global__ void __launch_bounds__(256)
             }
             cnt = box[a].count;
             mi = sminidx[a];
+            st_relaxed(parent + a, r);
         }
         uint32_t active = __ballot_sync(0xffffffffu, valid);
-        if (valid) st_relaxed(parent + a, r);
         while (active) {
             const int leader = __ffs(active) - 1;
             const uint32_t r0 = __shfl_sync(0xffffffffu, r, leader);
             const bool in = valid && r == r0;
-            const uint32_t s = __reduce_add_sync(0xffffffffu, in ? cnt : 0u);
+            const uint32_t sm = __reduce_add_sync(0xffffffffu, in ? cnt : 0u);
             const uint32_t mn = __reduce_min_sync(0xffffffffu, in ? mi : 0xffffffffu);
             if (lane == leader) {
-                atomicAdd(csize + r0, s);
-                atomicMin(cmin + r0, mn);
+                uint32_t slot = (r0 * 2654435761u) >> (32 - 9);
+                bool placed = false;
+                for (int probe = 0; probe < 8; ++probe) {
+                    const uint32_t cur = atomicCAS(&t_root[slot], 0xffffffffu, r0);
+                    if (cur == 0xffffffffu || cur == r0) {
+                        atomicAdd(&t_size[slot], sm);
+                        atomicMin(&t_min[slot], mn);
+                        placed = true;
+                        break;
+                    }
+                    slot = (slot + 1) & (kFlatSlots - 1);
+                }
+                if (!placed) {
+                    atomicAdd(csize + r0, sm);
+                    atomicMin(cmin + r0, mn);
+                }
             }
             active &= ~__ballot_sync(0xffffffffu, in);
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kFlatSlots; i += blockDim.x) {
+        const uint32_t r0 = t_root[i];
+        if (r0 == 0xffffffffu) continue;
+        atomicAdd(csize + r0, t_size[i]);
+        atomicMin(cmin + r0, t_min[i]);
     }
 }
 
