@@ -389,6 +389,8 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ uint32_t s_tile;
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_prefix;
+    __shared__ Rec s_rec[kScanTile];     // the tile's records, staged for coalesced stores
+    __shared__ uint32_t s_sc[kScanTile];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (;;) {
@@ -402,12 +404,23 @@ __global__ void __launch_bounds__(kScanThreads)
         unsigned long long flag[kScanIPT];  // (cell head << 31) | sub-cell head
         KeyT prev = (p0 > 0 && p0 - 1 < n) ? keys[p0 - 1] : KeyT(0);
         unsigned long long run = 0;
+        const bool full = p0 + kScanIPT <= n;
+        if (full) {  // the thread's keys in 16-byte loads
+            constexpr int per = 16 / sizeof(KeyT);
+#pragma unroll
+            for (int v = 0; v < kScanIPT / per; ++v) {
+                const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(keys + p0) + v);
+                const KeyT *e = reinterpret_cast<const KeyT *>(&w);
+#pragma unroll
+                for (int t = 0; t < per; ++t) k[v * per + t] = e[t];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
             const uint32_t p = p0 + i;
             unsigned long long f = 0;
             if (p < n) {
-                k[i] = keys[p];
+                if (!full) k[i] = keys[p];
                 const bool sh = (p == 0) || k[i] != prev;
                 const bool ch = (p == 0) || (k[i] >> 3) != (prev >> 3);
                 f = ((unsigned long long)ch << 31) | (unsigned long long)sh;
@@ -480,8 +493,19 @@ __global__ void __launch_bounds__(kScanThreads)
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
 
         ValT vv[kScanIPT];
+        if (full) {
+            constexpr int per = 16 / sizeof(ValT);
 #pragma unroll
-        for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : (ValT)0;
+            for (int v = 0; v < kScanIPT / per; ++v) {
+                const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(vals + p0) + v);
+                const ValT *e = reinterpret_cast<const ValT *>(&w);
+#pragma unroll
+                for (int t = 0; t < per; ++t) vv[v * per + t] = e[t];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : (ValT)0;
+        }
         unsigned long long before = base;
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
@@ -498,7 +522,7 @@ __global__ void __launch_bounds__(kScanThreads)
                 atomicOr(&plan->status, ST_SIZE_OVERFLOW);
                 continue;
             }
-            sc_of[p] = sc;
+            s_sc[tid * kScanIPT + i] = sc;
             if (sh) {
                 sc_start[sc] = p;
                 scode[sc] = (uint8_t)(k[i] & 7u);
@@ -520,13 +544,21 @@ __global__ void __launch_bounds__(kScanThreads)
                 quantize1(xyz[3 * (size_t)idx + 2], r.z);
             }
             r.idx = idx;
-            rec[p] = r;
+            s_rec[tid * kScanIPT + i] = r;
             if (p == n - 1) {
                 plan->M_s = sc + 1;
                 plan->M_c = c + 1;
                 sc_start[sc + 1] = n;
                 cell_sc[c + 1] = sc + 1;
             }
+        }
+        __syncthreads();
+        // the tile's records and sub-cell indices, written out coalesced
+        const uint32_t tile_n = min((uint32_t)kScanTile, n - tile * (uint32_t)kScanTile);
+        for (uint32_t j = tid; j < tile_n; j += kScanThreads) {
+            __stcs(reinterpret_cast<int4 *>(rec) + (size_t)tile * kScanTile + j,
+                   reinterpret_cast<const int4 *>(s_rec)[j]);
+            __stcs(sc_of + (size_t)tile * kScanTile + j, s_sc[j]);
         }
         __syncthreads();
     }
