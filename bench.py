@@ -36,16 +36,29 @@ UNIT = "Mpoints/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic DRAM bytes of one launch of each kernel, per unit it processes
-# (n = points, Ms = sub-cells, Mc = cells); compulsory traffic only.
+# (n = points, Ms = sub-cells, Mc = cells); compulsory traffic only (each
+# array the kernel must read or write, once):
+#   k_bbox           xyz 12
+#   k_keys           xyz 12 + key 4 + payload 8
+#   sort pass        (key 4 + payload 8) read and written
+#   k_cells          key + payload 12, record 16 + sub-cell of position 4 per point;
+#                    start 4 + code 1 per sub-cell; key 8 + first sub-cell 4 per cell
+#   k_subcell_stats  record 16 per point; start 4, box 32, smallest index 4,
+#                    representative 16, parent/size/min/rank 16 per sub-cell
+#   k_region         range 4, neighbour record 32, neighbour first sub-cells 52 per
+#                    cell; box 32, representative 16, parent 4 per sub-cell
+#   k_flatten_stats  parent 4+4, count 4, smallest index 4, size/min 8 per sub-cell
+#   k_labels         payload 8, sub-cell of position 4, label 4 per point;
+#                    sub-cell label 4 per sub-cell
 KERNEL_BYTES = {
     "k_bbox": lambda n, Ms, Mc: 12 * n,
-    "k_keys_u32": lambda n, Ms, Mc: 16 * n,
-    "onesweep_u32": lambda n, Ms, Mc: 16 * n,
-    "k_cells_u32": lambda n, Ms, Mc: 40 * n + 4 * Ms + 12 * Mc,
-    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 56 * Ms,
-    "k_region": lambda n, Ms, Mc: 76 * Mc + 60 * Ms,
+    "k_keys_u32": lambda n, Ms, Mc: 24 * n,
+    "onesweep_u32": lambda n, Ms, Mc: 24 * n,
+    "k_cells_u32": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
+    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 72 * Ms,
+    "k_region": lambda n, Ms, Mc: 88 * Mc + 52 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
-    "k_labels": lambda n, Ms, Mc: 12 * n,
+    "k_labels": lambda n, Ms, Mc: 16 * n + 4 * Ms,
 }
 KERNEL_SOURCE = {
     "k_bbox": "fec_grid.cu", "k_keys_u32": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
@@ -477,7 +490,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": cloud.d, "min_size": cloud.min_size,
                        "max_size": cloud.max_size, "num_clusters": int(k), "cells": Mc,
-                       "subcells": Ms, "l2": "input 335 MB > 126 MB L2, no flush",
+                       "subcells": Ms,
+                       "l2": f"input {12 * n / 1e6:.0f} MB > 126 MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": ms_e2e_max,
                     "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * n + 4},
