@@ -49,6 +49,7 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->M_s = 0;
         plan->M_c = 0;
         plan->n_big = 0;
+        plan->n_huge = 0;
         plan->scan_tile_counter = 0;
         plan->union_counter = 0;
         plan->pairq_n = 0;
@@ -618,7 +619,10 @@ __global__ void __launch_bounds__(256)
             continue;
         }
         if (e - s > (uint32_t)kBigSubcell) {
-            big[atomicAdd(&plan->n_big, 1u)] = a;
+            // medium sub-cells from the front of the list, huge ones from its middle
+            // (at most n/65 and n/2049 of them)
+            if (e - s > (uint32_t)kHugeSubcell) big[plan->sort.n / 2 + atomicAdd(&plan->n_huge, 1u)] = a;
+            else big[atomicAdd(&plan->n_big, 1u)] = a;
             continue;
         }
         SubBox b;
@@ -651,15 +655,72 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// a3: the same for the queued large sub-cells, one block per sub-cell.
+// a3: the same for the queued sub-cells of kBigSubcell..kHugeSubcell points,
+// one warp per sub-cell.
 __global__ void __launch_bounds__(256)
     k_subcell_big(Plan *plan, Params prm, const Rec *__restrict__ rec,
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
                   SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
 {
+    const uint32_t nb = plan->n_big;
+    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
+    const int l = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < nb; j += nwarps) {
+        const uint32_t a = big[j];
+        const uint32_t s = sc_start[a], e = sc_start[a + 1];
+        const Rec r0 = rec[s];
+        int32_t org[3], cen2[3];
+        const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
+        int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+        uint32_t mi = 0xffffffffu;
+        unsigned long long bk = ~0ull;
+        for (uint32_t p = s + l; p < e; p += 32) {
+            const Rec r = rec[p];
+            L[0] = min(L[0], r.x); H[0] = max(H[0], r.x);
+            L[1] = min(L[1], r.y); H[1] = max(H[1], r.y);
+            L[2] = min(L[2], r.z); H[2] = max(H[2], r.z);
+            mi = min(mi, r.idx);
+            const unsigned long long k =
+                ((unsigned long long)__float_as_uint(centre_dist2(r, org, cen2)) << 32) | (p - s);
+            bk = k < bk ? k : bk;
+        }
+#pragma unroll
+        for (int a3 = 0; a3 < 3; ++a3) {
+            L[a3] = warp_min(L[a3]);
+            H[a3] = warp_max(H[a3]);
+        }
+        mi = warp_min(mi);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, bk, o);
+            bk = u < bk ? u : bk;
+        }
+        if (l == 0) {
+            SubBox b;
+            b.lx = L[0]; b.ly = L[1]; b.lz = L[2];
+            b.hx = H[0]; b.hy = H[1]; b.hz = H[2];
+            b.start = s;
+            b.count = e - s;
+            box[a] = b;
+            sminidx[a] = mi;
+            reps[a] = rec[s + (uint32_t)bk];
+        }
+    }
+}
+
+// a3: the same for the queued sub-cells above kHugeSubcell points, one block per
+// sub-cell.
+__global__ void __launch_bounds__(256)
+    k_subcell_huge(Plan *plan, Params prm, const Rec *__restrict__ rec,
+                  const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
+{
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
-    const uint32_t nb = plan->n_big;
+    const uint32_t nb = plan->n_huge;
+    big += plan->sort.n / 2;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
@@ -835,6 +896,9 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
                                               ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_big", st);
+    k_subcell_huge<<<ws.sms * 2, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
+                                               ws.sminidx, ws.reps);
+    FEC_MARK(ws, "k_subcell_huge", st);
     e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ws.slab_hi, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);

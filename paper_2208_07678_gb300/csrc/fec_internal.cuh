@@ -65,7 +65,8 @@ constexpr int kSortTile = kSortThreads * kSortIPT;   // 4096 keys per tile
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
-constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a block
+constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a warp,
+constexpr int kHugeSubcell = 2048;       //   above this size by a block
 constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept per block
 #ifndef FEC_REGION_CELLS
 #define FEC_REGION_CELLS 1024
@@ -100,7 +101,8 @@ struct Plan {
     uint32_t key_bits;         // total sort-key bits (cell key bits + 3)
     uint32_t status;           // ST_* bits
     uint32_t M_s, M_c;         // occupied sub-cells and cells
-    uint32_t n_big;            // sub-cells with more than kBigSubcell points
+    uint32_t n_big;            // sub-cells with more than kBigSubcell points (up to kHugeSubcell)
+    uint32_t n_huge;           // sub-cells with more than kHugeSubcell points
     uint32_t scan_tile_counter;
     uint32_t union_counter;     // dynamic cell chunks of the union step
     uint32_t pairq_n;           // pairs queued for point-level tests
