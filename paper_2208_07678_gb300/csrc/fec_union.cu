@@ -359,10 +359,11 @@ __global__ void __launch_bounds__(256, 4)
 constexpr int kRegionCells = (int)kRegionCellsPerBlock;
 constexpr int kRegionWarps = kRegionThreads / 32;
 constexpr int kRegionSubs = 8 * kRegionCells;
+static_assert(kRegionSubs <= 65536, "region-local sub-cell indices are 16-bit");
 constexpr int kRegionBuf = 512;
 
 struct RegionSmem {
-    uint32_t par[kRegionSubs];
+    uint16_t par[kRegionSubs];             // union-find parent, region-local (< 2^16)
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
     uint32_t ecount, qcount, next, region, pad[4];
@@ -376,7 +377,7 @@ struct RegionSmem {
     uint32_t qb[kRegionWarps][64];
 };
 
-__device__ __forceinline__ uint32_t s_find(volatile uint32_t *par, uint32_t x)
+__device__ __forceinline__ uint32_t s_find(volatile uint16_t *par, uint32_t x)
 {
     for (;;) {
         const uint32_t p = par[x];
@@ -388,9 +389,9 @@ __device__ __forceinline__ uint32_t s_find(volatile uint32_t *par, uint32_t x)
     }
 }
 
-__device__ __forceinline__ void s_unite(uint32_t *par, uint32_t a, uint32_t b)
+__device__ __forceinline__ void s_unite(uint16_t *par, uint32_t a, uint32_t b)
 {
-    volatile uint32_t *vp = par;
+    volatile uint16_t *vp = par;
     for (;;) {
         a = s_find(vp, a);
         b = s_find(vp, b);
@@ -400,7 +401,8 @@ __device__ __forceinline__ void s_unite(uint32_t *par, uint32_t a, uint32_t b)
             a = b;
             b = t;
         }
-        const uint32_t old = atomicCAS(par + a, a, b);
+        const uint32_t old = atomicCAS(reinterpret_cast<unsigned short *>(par + a), (unsigned short)a,
+                                       (unsigned short)b);
         if (old == a) return;
         a = old;
     }
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     m.R1 = prm.R + 1;
     uint32_t n_pairs = 0, n_yes = 0, n_und = 0, n_same = 0, n_queued = 0, n_edges = 0;
     unsigned long long n_evals = 0;
-    volatile uint32_t *vpar = S.par;
+    volatile uint16_t *vpar = S.par;
     // this block's list of undecided in-region pairs (local indices a | b << 16
     // would not fit 8192 sub-cells twice, so two u16 halves of a u32: a, b < 8192)
     uint32_t *const my_scratch = scratch + (size_t)blockIdx.x * scap;
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         if (r >= nregions) break;
         const uint32_t c_lo = r * kRegionCells, c_hi = min(c_lo + kRegionCells, M);
         const uint32_t s0 = cell_sc[c_lo], s1 = cell_sc[c_hi], ns = s1 - s0;
-        for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = i;
+        for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = (uint16_t)i;
         for (int i = tid; i < kRegionBuf; i += blockDim.x) {
             S.ebuf[i] = make_uint2(0xffffffffu, 0xffffffffu);
             S.qbuf[i] = make_uint2(0xffffffffu, 0xffffffffu);
