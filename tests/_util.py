@@ -144,3 +144,36 @@ def random_cloud(seed, n, extent=4.0, clumps=0):
     else:
         pts = rng.uniform(0, extent, size=(n, 3))
     return (np.rint(pts * 1024) / 1024).astype(np.float32)
+
+
+def boundary_pairs(d, seed):
+    """Isolated point pairs at squared distances within a few units of T2
+    (both sides), with random alignment to the cell and sub-cell grid, plus
+    axis-aligned pairs at exactly R and R+1 in all six directions.  Pairs sit
+    5d apart, so only the two points of a pair can join."""
+    rng = np.random.default_rng(seed)
+    T2 = threshold_np(d)
+    R = int(np.floor(np.sqrt(T2)))
+    while R * R > T2:
+        R -= 1
+    while (R + 1) * (R + 1) <= T2:
+        R += 1
+    step = int(5 * d * 1024)
+    g = np.arange(24)
+    centres = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * step
+    centres += rng.integers(0, max(1, step // 5), size=centres.shape)
+    m = len(centres)
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    length = np.sqrt(T2) + rng.uniform(-1.5, 1.5, size=(m, 1))
+    off = np.rint(u * length).astype(np.int64)
+    axis = np.zeros((12, 3), np.int64)
+    for i in range(6):
+        axis[2 * i, i // 2] = (R if i % 2 == 0 else -R)
+        axis[2 * i + 1, i // 2] = (R + 1 if i % 2 == 0 else -(R + 1))
+    off[: len(axis)] = axis
+    q = np.concatenate([centres, centres + off])
+    xyz = (q / 1024.0).astype(np.float32)
+    joined = (off * off).sum(1) <= T2
+    return xyz, joined
+

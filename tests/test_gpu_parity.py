@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2208_07678_gb300 import fec, synth
-from tests._util import INT64_MAX, check_labels_valid, fixtures, random_cloud
+from tests._util import INT64_MAX, boundary_pairs, check_labels_valid, fixtures, random_cloud
 
 pytestmark = pytest.mark.gpu
 
@@ -235,3 +235,17 @@ def test_stats(ctx):
     s = ctx.stats()
     assert s["n"] == c.n and 0 < s["cells"] <= s["subcells"] <= c.n
     assert s["R"] == 358 and s["h"] == 179 and s["T2"] == oracle.threshold(c.d)
+
+
+@pytest.mark.parametrize("d", [0.05, 0.2, 0.35, 1.0, 3.0])
+def test_pairs_across_cell_and_subcell_boundaries(ctx, d):
+    """Exercises the geometric shortcuts of the union step (sub-cell cliques,
+    the rule that sub-cells three sub-cell steps apart cannot join, box and
+    representative tests) exactly at the threshold: every pair must be
+    joined iff its squared distance is at most T2."""
+    xyz, joined = boundary_pairs(d, seed=int(d * 1000))
+    got, k = assert_parity(ctx, xyz, d)
+    m = len(joined)
+    assert k == int(joined.sum()) + 2 * int((~joined).sum())
+    same = got[:m] == got[m:]
+    np.testing.assert_array_equal(same, joined)

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from oracle.paper_fec import canonical, paper_fec_serial
 from paper_2208_07678_gb300 import synth
-from tests._util import (INT64_MAX, check_labels_valid, fixtures, quantize_np,
+from tests._util import (INT64_MAX, boundary_pairs, check_labels_valid, fixtures, quantize_np,
                          random_cloud, scipy_labels, threshold_np)
 
 FIXTURES = fixtures()
@@ -203,3 +203,17 @@ def test_planted_mistake_is_caught():
     assert not strict  # the strict reading would split the pair
     lab, k = oracle.cluster(fx["xyz"], fx["d"])
     assert k == 1
+
+
+@pytest.mark.parametrize("d", [0.05, 0.35, 3.0])
+def test_pairs_at_the_threshold(d):
+    """Closed form: isolated pairs (5d apart) join iff their squared distance
+    in quantised units is at most T2 = floor((d*1024)^2) (Eq. 1 with the
+    quantisation reading); pairs sit within a few units of T2 on both sides,
+    including axis-aligned pairs at exactly R and R + 1."""
+    xyz, joined = boundary_pairs(d, seed=int(d * 1000) + 1)
+    labels, k = oracle.cluster(xyz, d, 1, INT64_MAX)
+    m = len(joined)
+    assert k == int(joined.sum()) + 2 * int((~joined).sum())
+    np.testing.assert_array_equal(labels[:m] == labels[m:], joined)
+
