@@ -306,6 +306,63 @@ def measure_batch(fec, torch, dev, stream, steps, seed=4):
             "labels_equal_plain": same}
 
 
+def measure_frame(fec, torch, dev, stream, steps=20):
+    """Mpoints/s on the single 120k-point frame (one fec_cluster call per
+    step, device-resident input and output)."""
+    from paper_2208_07678_gb300 import synth
+
+    c = synth.frame_120k()
+    xyz = torch.from_numpy(c.xyz).to(dev)
+    lab = torch.empty(c.n, dtype=torch.int32, device=dev)
+    with fec.Context(device=dev.index, cuda_stream=stream.cuda_stream) as fctx:
+        for _ in range(5):
+            _, k = fctx.cluster(xyz, c.d, c.min_size, c.max_size, labels=lab)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fctx.cluster(xyz, c.d, c.min_size, c.max_size, labels=lab)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+    return {"n": c.n, "d": c.d, "min_size": c.min_size, "max_size": c.max_size, "k": int(k),
+            "ms": round(ms, 4), "Mpoints_per_s": round(c.n / ms / 1e3, 1)}
+
+
+def measure_voxel_sweep(fec, torch, dev, stream, steps=5):
+    """The synthetic sweeps of Section 3.3.1 as scaling evidence: m points
+    filled evenly into n random voxels (clusters; unit voxels, never
+    touching), optionally shifted by N(0, sigma); d = 0.5.  Device time per
+    fec_cluster call over density x cluster count, and over sigma at 1,000
+    clusters of 200 points.  The cluster count is checked against the
+    construction (every voxel one cluster while sigma = 0)."""
+    from paper_2208_07678_gb300 import synth
+
+    configs = [(nc, m, 0.0) for nc in (100, 1000, 2200) for m in (10, 100, 500)]
+    configs += [(1000, 200, s) for s in (0.05, 0.1, 0.2)]
+    rows = []
+    with fec.Context(device=dev.index, cuda_stream=stream.cuda_stream) as vctx:
+        for nc, m, sigma in configs:
+            xyz = torch.from_numpy(synth.voxel_clusters(7, nc, m, sigma=sigma)).to(dev)
+            lab = torch.empty(xyz.shape[0], dtype=torch.int32, device=dev)
+            for _ in range(3):
+                _, k = vctx.cluster(xyz, 0.5, 1, (1 << 63) - 1, labels=lab)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                vctx.cluster(xyz, 0.5, 1, (1 << 63) - 1, labels=lab)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            n = int(xyz.shape[0])
+            rows.append({"clusters": nc, "density": m, "sigma": sigma, "n": n, "k": int(k),
+                         "k_expected": nc if sigma == 0.0 else None, "ms": round(ms, 4),
+                         "Mpoints_per_s": round(n / ms / 1e3, 1)})
+    return {"d": 0.5, "voxel_m": 1.0, "rows": rows,
+            "note": "device-resident input, one fec_cluster call per step"}
+
+
 def measure_serve(fec, duration=4.0, rate=400.0, pool=40, seed=5, slots_note="4 worker slots"):
     """Serving: Poisson arrivals of request clouds (10k-2M points) with
     per-request d and size bounds; latency = completion - arrival.  Beside
@@ -472,7 +529,9 @@ def run_ours(args):
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
+        extra["frame_120k"] = measure_frame(fec, torch, dev, stream)
         extra["batch_256"] = measure_batch(fec, torch, dev, stream, max(3, args.steps))
+        extra["voxel_sweep"] = measure_voxel_sweep(fec, torch, dev, stream)
         extra["serve"] = measure_serve(fec, duration=args.serve_seconds)
         extra["serve_heavy"] = measure_serve(fec, duration=max(1.0, args.serve_seconds / 2),
                                              rate=2000.0)

@@ -131,7 +131,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.edge_set = (unsigned long long *)take(sizeof(unsigned long long) * es);
     ws.nb_first = (uint32_t *)take(4 * 13 * n);
     ws.nb_cnt = (uint8_t *)take(32 * n);
-    ws.scratch_words = (size_t)region_grid(ws, n) * kRegionScratch;
+    ws.scratch_words = (size_t)region_grid(ws, n) * region_scratch(ws, n);
     ws.scratch = (uint32_t *)take(4 * ws.scratch_words);
     off = (off + 255) & ~(size_t)255;
     if (base) {

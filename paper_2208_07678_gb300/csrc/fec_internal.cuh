@@ -308,13 +308,29 @@ struct Workspace {
 void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
 #define FEC_MARK(ws, name, st) trace_mark((ws), (name), (st))
 
-// Blocks of the region kernel for n points (at most 3 per SM, at most one per
-// possible region).
+// Regions have kRegionCellsPerBlock cells, fewer (down to kRegionMinCells)
+// when the cloud has too few cells to give every block of the grid two.
+constexpr uint32_t kRegionMinCells = 64;
+
+// Blocks of the region kernel for n points (kRegionBlocksPerSM per SM, at most
+// one per possible region of the smallest size).
 inline uint32_t region_grid(const Workspace &ws, uint64_t n)
 {
-    const uint64_t regions = (n + kRegionCellsPerBlock - 1) / kRegionCellsPerBlock;
+    const uint64_t regions = (n + kRegionMinCells - 1) / kRegionMinCells;
     const uint64_t g = (uint64_t)ws.sms * kRegionBlocksPerSM;
     return (uint32_t)(regions < g ? (regions ? regions : 1) : g);
+}
+
+// Scratch entries of each region block (undecided pairs inside its region):
+// kRegionScratch for full-size regions, in proportion for the smaller regions
+// a cloud of n points can get.
+inline uint32_t region_scratch(const Workspace &ws, uint64_t n)
+{
+    const uint64_t g = region_grid(ws, n);
+    uint64_t rc = n / (2 * g);
+    if (rc < kRegionMinCells) rc = kRegionMinCells;
+    if (rc > kRegionCellsPerBlock) rc = kRegionCellsPerBlock;
+    return (uint32_t)(kRegionScratch * rc / kRegionCellsPerBlock);
 }
 
 // Bytes of a workspace for cap_n points and slab_cap slab entries; with a

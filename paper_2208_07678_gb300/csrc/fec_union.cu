@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(256, 4)
 
 // ---------------------------------------------------------------------------
 // a4: region-local connectivity.  A block takes a region of kRegionCells
-// consecutive cells (in key order, i.e. a compact piece of space) and keeps a
+// consecutive cells (fewer when the cloud is small, so that every block gets
+// work; in key order, i.e. a compact piece of space) and keeps a
 // union-find over the region's sub-cells in shared memory.  Its warps take
 // the region's cells one at a time and decide sub-cell pairs 32 at a time:
 // the cell's own pairs and its half-stencil neighbour pairs (13 of the 26
@@ -449,7 +450,10 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     extern __shared__ __align__(16) unsigned char region_smem[];
     RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
     const uint32_t M = plan->M_c;
-    const uint32_t nregions = (M + kRegionCells - 1) / kRegionCells;
+    // region size: kRegionCells, or fewer cells when the cloud has too few
+    // cells to give every block two regions
+    const uint32_t rc = min((uint32_t)kRegionCells, max(kRegionMinCells, M / (2u * gridDim.x)));
+    const uint32_t nregions = (M + rc - 1) / rc;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     uint32_t *status = &plan->status;
     Metric<WIDE> m;
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         __syncthreads();
         const uint32_t r = S.region;
         if (r >= nregions) break;
-        const uint32_t c_lo = r * kRegionCells, c_hi = min(c_lo + kRegionCells, M);
+        const uint32_t c_lo = r * rc, c_hi = min(c_lo + rc, M);
         const uint32_t s0 = cell_sc[c_lo], s1 = cell_sc[c_hi], ns = s1 - s0;
         for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = (uint16_t)i;
         for (int i = tid; i < kRegionBuf; i += blockDim.x) {
@@ -1005,7 +1009,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
                                         ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
-    const uint32_t scap = kRegionScratch;
+    const uint32_t scap = region_scratch(ws, ws.cap_n);
     if (!wide)
         k_region<false><<<rgrid, kRegionThreads, smem, st>>>(
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
