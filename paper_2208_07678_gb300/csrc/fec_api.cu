@@ -182,7 +182,7 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
                         kp, sort_grid, st, &ws.plan->status);
         if (e != cudaSuccess) return e;
     }
-    return enqueue_labels(ws, labels, prm.packed != 0, st);
+    return enqueue_labels(ws, prm, labels, prm.packed != 0, st);
 }
 
 // Small summary of a finished call, packed on the device for one copy.

@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
 {
-    const int grid = ws.sms * 8;
+    const int grid = grid_for(ws, prm.n, 1024, 8);  // four points per thread
     k_init<<<1, 256, 0, st>>>(ws.plan, prm.n, (uint32_t)kept_sort_passes(prm.n));
     FEC_MARK(ws, "k_init", st);
     k_bbox<<<grid, 256, 0, st>>>(xyz, prm.n, ws.plan);
@@ -865,7 +865,8 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     cudaError_t e = cudaMemsetAsync(ws.scan_status, 0, (ntiles + 1) * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_scan_status", st);
-    const int grid = ws.sms * 8;
+    const int grid = grid_for(ws, prm.n, kScanTile, 8);
+    const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item per thread
     using u32 = uint32_t;
     using u64 = unsigned long long;
     if (prm.packed) {
@@ -890,13 +891,13 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
             ws.scan_status);
     }
     FEC_MARK(ws, "k_cells_u64", st);
-    k_subcell_stats<<<grid, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
+    k_subcell_stats<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);
     FEC_MARK(ws, "k_subcell_stats", st);
-    k_subcell_big<<<ws.sms * 4, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
+    k_subcell_big<<<grid_for(ws, prm.n / (kBigSubcell + 1), 8, 4), 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
                                               ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_big", st);
-    k_subcell_huge<<<ws.sms * 2, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
+    k_subcell_huge<<<grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2), 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
                                                ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_huge", st);
     e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
@@ -904,9 +905,9 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     e = cudaMemsetAsync(ws.slab_hi, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_slabs", st);
-    k_clear_cols<<<grid, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
+    k_clear_cols<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
     FEC_MARK(ws, "k_clear_cols", st);
-    k_slabs<<<grid, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
+    k_slabs<<<grid1, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
                                   ws.col_lo, ws.col_hi, ws.cocc);
     FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();

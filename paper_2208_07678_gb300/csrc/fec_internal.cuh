@@ -308,6 +308,15 @@ struct Workspace {
 void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
 #define FEC_MARK(ws, name, st) trace_mark((ws), (name), (st))
 
+// Blocks of a grid-stride kernel over `items` work items, `per_block` per
+// block and step: as many as the items need, at most `per_sm` per SM.
+inline int grid_for(const Workspace &ws, uint64_t items, uint64_t per_block, int per_sm)
+{
+    const uint64_t want = (items + per_block - 1) / per_block;
+    const uint64_t cap = (uint64_t)ws.sms * (uint64_t)per_sm;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
 // Regions have kRegionCellsPerBlock cells, fewer (down to kRegionMinCells)
 // when the cloud has too few cells to give every block of the grid two.
 constexpr uint32_t kRegionMinCells = 64;
@@ -352,7 +361,8 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
 cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
                           long long max_size, cudaStream_t st);
 // a6 rank + labels (labels: device pointer, n entries).
-cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, bool packed, cudaStream_t st);
+cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool packed,
+                           cudaStream_t st);
 // The whole pipeline for one cloud (device pointers), no host synchronisation.
 cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
                             long long min_size, long long max_size, int32_t *labels,

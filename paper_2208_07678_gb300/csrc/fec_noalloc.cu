@@ -126,7 +126,7 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
                             ws.kept_key_b(), ws.kept_val_b(), false, false, false,
                             ws.sort_status, un, kp, ws.sms, st, &ws.plan->status);
     }
-    if (e == cudaSuccess) e = enqueue_labels(ws, lout, pk, st);
+    if (e == cudaSuccess) e = enqueue_labels(ws, prm, lout, pk, st);
     if (e == cudaSuccess && !dev_out)
         e = cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
     uint32_t status_bits = 0, k = 0;

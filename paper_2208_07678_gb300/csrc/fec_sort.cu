@@ -242,6 +242,8 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     grid *= per_sm;
+    const int tiles = (int)(((uint64_t)max_n + kSortTile - 1) / kSortTile);
+    if (grid > tiles) grid = tiles > 0 ? tiles : 1;  // a small sort needs fewer blocks
     const size_t tstride = sort_status_words(max_n) / 2;
     cudaError_t e = cudaMemsetAsync(tile_status, 0, tstride * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;

@@ -1005,7 +1005,8 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
         cudaFuncSetAttribute(k_region<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_nbrs<<<ws.sms * 8, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
+    const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item (cell, sub-cell, edge) per thread
+    k_nbrs<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
                                         ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
@@ -1022,34 +1023,36 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     cudaError_t e = cudaMemsetAsync(ws.edge_set, 0xff, sizeof(unsigned long long) * ws.edge_set_size, st);
     if (e != cudaSuccess) return e;
     FEC_MARK(ws, "memset_edge_set", st);
-    k_edges<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
+    k_edges<<<grid1, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
                                         (uint32_t)(ws.edge_set_size - 1));
     FEC_MARK(ws, "k_edges", st);
     if (!wide)
-        k_pairs<false><<<ws.sms * 2, kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
+        k_pairs<false><<<grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                              ws.pairq, qcap);
     else
-        k_pairs<true><<<ws.sms * 2, kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
+        k_pairs<true><<<grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                             ws.pairq, qcap);
     FEC_MARK(ws, "k_pairs", st);
-    k_flatten_stats<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
+    k_flatten_stats<<<grid1, 256, 0, st>>>(ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
                                                  ws.cmin);
     FEC_MARK(ws, "k_flatten_stats", st);
-    k_kept<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, min_size, max_size,
+    k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, min_size, max_size,
                                         ws.kept_key_a(), ws.kept_val_a());
     FEC_MARK(ws, "k_kept", st);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_labels(Workspace &ws, int32_t *labels, bool packed, cudaStream_t st)
+cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool packed,
+                           cudaStream_t st)
 {
-    k_rank<<<ws.sms * 4, 256, 0, st>>>(ws.plan, ws.kept_val_a(), ws.kept_val_b(), ws.crank);
+    const int grid1 = grid_for(ws, prm.n, 256, 8);
+    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_val_a(), ws.kept_val_b(), ws.crank);
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
     int32_t *sclab = (int32_t *)ws.csize;  // component sizes are no longer needed
-    k_sclabel<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab);
+    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab);
     FEC_MARK(ws, "k_sclabel", st);
-    k_labels<<<ws.sms * 8, 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
+    k_labels<<<grid_for(ws, prm.n, 2048, 8), 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
                                          (const uint32_t *)ws.vals_b, packed ? 2u : 1u, ws.sc_of,
                                          sclab, labels);
     FEC_MARK(ws, "k_labels", st);
