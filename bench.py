@@ -52,17 +52,17 @@ FALLBACK_HBM_GBS = 6800.0
 #                    sub-cell label 4 per sub-cell
 KERNEL_BYTES = {
     "k_bbox": lambda n, Ms, Mc: 12 * n,
-    "k_keys_u32": lambda n, Ms, Mc: 24 * n,
+    "k_keys": lambda n, Ms, Mc: 24 * n,
     "onesweep_u32": lambda n, Ms, Mc: 24 * n,
-    "k_cells_u32": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
+    "k_cells": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
     "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 72 * Ms,
     "k_region": lambda n, Ms, Mc: 88 * Mc + 52 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
     "k_labels": lambda n, Ms, Mc: 16 * n + 4 * Ms,
 }
 KERNEL_SOURCE = {
-    "k_bbox": "fec_grid.cu", "k_keys_u32": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
-    "k_cells_u32": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_region": "fec_union.cu",
+    "k_bbox": "fec_grid.cu", "k_keys": "fec_grid.cu", "onesweep_u32": "fec_sort.cu",
+    "k_cells": "fec_grid.cu", "k_subcell_stats": "fec_grid.cu", "k_region": "fec_union.cu",
     "k_flatten_stats": "fec_union.cu", "k_labels": "fec_union.cu",
 }
 HOUSEKEEPING = ("memset", "h2d", "d2h", "summary")

@@ -60,9 +60,11 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->sort.n = n;
         plan->sort.npasses = 0;
         plan->sort.key64 = 0;
+        plan->sort.parity = 0;
         plan->kept.n = 0;
         plan->kept.npasses = kept_passes;
         plan->kept.key64 = 0;
+        plan->kept.parity = 0;
     }
     for (int i = t; i < kMaxPasses * kRadixBins; i += blockDim.x) {
         (&plan->sort.hist[0][0])[i] = 0;
@@ -191,6 +193,7 @@ __global__ void k_plan(Plan *plan, Params prm)
     plan->use_cols = (plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
     plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
     plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
+    plan->kept.parity = plan->sort.npasses & 1u;  // the look-back array the main sort leaves clear
 }
 
 // Element i (0..2) of a 3-vector held in registers (no local-memory indexing).
@@ -271,19 +274,38 @@ struct GridMap {
     }
 };
 
+// Arrays zeroed by the key kernel for the later stages.
+struct Clears {
+    uint32_t *sort_status;          // look-back array 0 of the main sort
+    size_t sort_words;
+    unsigned long long *scan_status;  // cell-table look-back
+    size_t scan_words;
+    uint32_t *slab_lo, *slab_hi;    // slab index
+    size_t slab_words;
+    size_t max_words;
+};
+
 // a1: grid keys of all points, plus the digit histograms of every radix pass.
 template <typename KeyT, bool PACKED>
-__global__ void __launch_bounds__(256)
-    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, KeyT *__restrict__ keys,
-           unsigned long long *__restrict__ vals)
+__device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *plan, const Params &prm,
+                                          KeyT *__restrict__ keys,
+                                          unsigned long long *__restrict__ vals, const Clears &clr,
+                                          uint32_t (*h)[kRadixBins])
 {
-    constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
     SortCtl *ctl = &plan->sort;
-    if (ctl->key64 != want64) return;
     const uint32_t n = ctl->n;
     if (n == 0) return;
+    // arrays the later stages need zeroed (in place of separate memsets)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < clr.max_words;
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (i < clr.sort_words) clr.sort_status[i] = 0;
+        if (i < clr.scan_words) clr.scan_status[i] = 0;
+        if (i < clr.slab_words) {
+            clr.slab_lo[i] = 0;
+            clr.slab_hi[i] = 0;
+        }
+    }
     const int np = (int)ctl->npasses;
-    __shared__ uint32_t h[kMaxPasses][kRadixBins];
     for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
     GridMap g;
     g.load(plan, prm);
@@ -356,6 +378,19 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The key kernel for either key width (the plan selects it on the device).
+template <bool PACKED>
+__global__ void __launch_bounds__(256)
+    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, void *__restrict__ keys,
+           unsigned long long *__restrict__ vals, Clears clr)
+{
+    __shared__ uint32_t h[kMaxPasses][kRadixBins];
+    if (plan->sort.key64)
+        keys_body<unsigned long long, PACKED>(xyz, plan, prm, (unsigned long long *)keys, vals, clr, h);
+    else
+        keys_body<uint32_t, PACKED>(xyz, plan, prm, (uint32_t *)keys, vals, clr, h);
+}
+
 // a3: cell table from the sorted keys, in one pass with a decoupled look-back
 // scan of two head flags (new sub-cell, new cell).  Also gathers the sorted
 // point records (quantised coordinates + original index).
@@ -363,18 +398,27 @@ __global__ void __launch_bounds__(256)
 //   sc_start[a]   first sorted position of sub-cell a (sc_start[M_s] = n)
 //   scode[a]      sub-cell code of a: which half of its cell on each axis
 //   cell_key[c]   cell key of cell c; cell_sc[c] first sub-cell of cell c
+struct CellsSmem {
+    uint32_t tile;
+    unsigned long long warp[kScanThreads / 32];
+    unsigned long long prefix;
+    Rec rec[kScanTile];     // the tile's records, staged for coalesced stores
+    uint32_t sc[kScanTile];
+};
+
 template <typename KeyT, typename ValT>
-__global__ void __launch_bounds__(kScanThreads)
-    k_cells(Plan *plan, Params prm, const KeyT *__restrict__ keys_a, const ValT *__restrict__ vals_a,
-            const KeyT *__restrict__ keys_b, const ValT *__restrict__ vals_b,
-            const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
-            uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
-            unsigned long long *__restrict__ cell_key,
-            uint32_t *__restrict__ cell_sc, unsigned long long *__restrict__ tstat)
+__device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const KeyT *__restrict__ keys_a,
+                                           const ValT *__restrict__ vals_a,
+                                           const KeyT *__restrict__ keys_b,
+                                           const ValT *__restrict__ vals_b,
+                                           const float *__restrict__ xyz, Rec *__restrict__ rec,
+                                           uint32_t *__restrict__ sc_of,
+                                           uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
+                                           unsigned long long *__restrict__ cell_key,
+                                           uint32_t *__restrict__ cell_sc,
+                                           unsigned long long *__restrict__ tstat, CellsSmem &C)
 {
-    constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
     const SortCtl *ctl = &plan->sort;
-    if (ctl->key64 != want64) return;
     const uint32_t n = ctl->n;
     if (n == 0) return;
     const bool in_b = (ctl->npasses & 1u) != 0;
@@ -387,11 +431,11 @@ __global__ void __launch_bounds__(kScanThreads)
 
     constexpr unsigned long long kAgg = 1ull << 62, kIncl = 2ull << 62;
     constexpr unsigned long long kMask = (1ull << 62) - 1;
-    __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    __shared__ unsigned long long s_prefix;
-    __shared__ Rec s_rec[kScanTile];     // the tile's records, staged for coalesced stores
-    __shared__ uint32_t s_sc[kScanTile];
+    uint32_t &s_tile = C.tile;
+    unsigned long long *s_warp = C.warp;
+    unsigned long long &s_prefix = C.prefix;
+    Rec *s_rec = C.rec;
+    uint32_t *s_sc = C.sc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (;;) {
@@ -563,6 +607,28 @@ __global__ void __launch_bounds__(kScanThreads)
         }
         __syncthreads();
     }
+}
+
+// The cell-table kernel for either key width (the plan selects it on the
+// device); the payload width is known on the host.
+template <typename ValT>
+__global__ void __launch_bounds__(kScanThreads, 4)
+    k_cells(Plan *plan, Params prm, const void *__restrict__ keys_a, const ValT *__restrict__ vals_a,
+            const void *__restrict__ keys_b, const ValT *__restrict__ vals_b,
+            const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
+            uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
+            unsigned long long *__restrict__ cell_key, uint32_t *__restrict__ cell_sc,
+            unsigned long long *__restrict__ tstat)
+{
+    __shared__ CellsSmem C;
+    using u64 = unsigned long long;
+    if (plan->sort.key64)
+        cells_body<u64, ValT>(plan, prm, (const u64 *)keys_a, vals_a, (const u64 *)keys_b, vals_b, xyz,
+                              rec, sc_of, sc_start, scode, cell_key, cell_sc, tstat, C);
+    else
+        cells_body<uint32_t, ValT>(plan, prm, (const uint32_t *)keys_a, vals_a,
+                                   (const uint32_t *)keys_b, vals_b, xyz, rec, sc_of, sc_start,
+                                   scode, cell_key, cell_sc, tstat, C);
 }
 
 // The nominal (grid) centre of the sub-cell containing q, as the cell origin
@@ -844,53 +910,40 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cu
     k_plan<<<1, 32, 0, st>>>(ws.plan, prm);
     FEC_MARK(ws, "k_plan", st);
     auto *va = (unsigned long long *)ws.vals_a;
-    if (prm.packed) {
-        k_keys<uint32_t, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a, va);
-        FEC_MARK(ws, "k_keys_u32", st);
-        k_keys<unsigned long long, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm,
-                                                              (unsigned long long *)ws.keys_a, va);
-    } else {
-        k_keys<uint32_t, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, (uint32_t *)ws.keys_a, va);
-        FEC_MARK(ws, "k_keys_u32", st);
-        k_keys<unsigned long long, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm,
-                                                               (unsigned long long *)ws.keys_a, va);
-    }
-    FEC_MARK(ws, "k_keys_u64", st);
+    Clears clr;
+    clr.sort_status = ws.sort_status;
+    clr.sort_words = sort_status_words(prm.n) / 2;
+    clr.scan_status = ws.scan_status;
+    clr.scan_words = (size_t)prm.n / kScanTile + 2;
+    clr.slab_lo = ws.slab_lo;
+    clr.slab_hi = ws.slab_hi;
+    clr.slab_words = prm.slab_cap;
+    clr.max_words = clr.sort_words > clr.scan_words ? clr.sort_words : clr.scan_words;
+    if (clr.slab_words > clr.max_words) clr.max_words = clr.slab_words;
+    if (prm.packed)
+        k_keys<true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+    else
+        k_keys<false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+    FEC_MARK(ws, "k_keys", st);
     return cudaGetLastError();
 }
 
 cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
 {
-    const size_t ntiles = ((size_t)prm.n + kScanTile - 1) / kScanTile;
-    cudaError_t e = cudaMemsetAsync(ws.scan_status, 0, (ntiles + 1) * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    FEC_MARK(ws, "memset_scan_status", st);
+    // the look-back status and the slab index were cleared by the key kernel
     const int grid = grid_for(ws, prm.n, kScanTile, 8);
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item per thread
     using u32 = uint32_t;
     using u64 = unsigned long long;
-    if (prm.packed) {
-        k_cells<u32, u64><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, (const u32 *)ws.keys_a, (const u64 *)ws.vals_a, (const u32 *)ws.keys_b,
-            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
-            ws.scan_status);
-        FEC_MARK(ws, "k_cells_u32", st);
-        k_cells<u64, u64><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, (const u64 *)ws.keys_a, (const u64 *)ws.vals_a, (const u64 *)ws.keys_b,
-            (const u64 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
-            ws.scan_status);
-    } else {
-        k_cells<u32, u32><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, (const u32 *)ws.keys_a, (const u32 *)ws.vals_a, (const u32 *)ws.keys_b,
-            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
-            ws.scan_status);
-        FEC_MARK(ws, "k_cells_u32", st);
-        k_cells<u64, u32><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, (const u64 *)ws.keys_a, (const u32 *)ws.vals_a, (const u64 *)ws.keys_b,
-            (const u32 *)ws.vals_b, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc,
-            ws.scan_status);
-    }
-    FEC_MARK(ws, "k_cells_u64", st);
+    if (prm.packed)
+        k_cells<u64><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, ws.keys_a, (const u64 *)ws.vals_a, ws.keys_b, (const u64 *)ws.vals_b, xyz,
+            ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc, ws.scan_status);
+    else
+        k_cells<u32><<<grid, kScanThreads, 0, st>>>(
+            ws.plan, prm, ws.keys_a, (const u32 *)ws.vals_a, ws.keys_b, (const u32 *)ws.vals_b, xyz,
+            ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc, ws.scan_status);
+    FEC_MARK(ws, "k_cells", st);
     k_subcell_stats<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);
     FEC_MARK(ws, "k_subcell_stats", st);
@@ -900,11 +953,6 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     k_subcell_huge<<<grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2), 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
                                                ws.sminidx, ws.reps);
     FEC_MARK(ws, "k_subcell_huge", st);
-    e = cudaMemsetAsync(ws.slab_lo, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(ws.slab_hi, 0, (size_t)prm.slab_cap * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    FEC_MARK(ws, "memset_slabs", st);
     k_clear_cols<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
     FEC_MARK(ws, "k_clear_cols", st);
     k_slabs<<<grid1, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,

@@ -88,7 +88,7 @@ struct SortCtl {
     uint32_t n;         // number of keys
     uint32_t npasses;   // 8-bit digit passes to run
     uint32_t key64;     // 1: 64-bit keys, 0: 32-bit keys
-    uint32_t pad;
+    uint32_t parity;    // pass p uses look-back array (p + parity) & 1, which starts clear
     uint32_t hist[kMaxPasses][kRadixBins];   // digit counts of every pass
     uint32_t tile_counter[kMaxPasses];       // dynamic tile ids of every pass
 };

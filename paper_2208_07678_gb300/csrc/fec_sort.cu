@@ -71,10 +71,11 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     // Two look-back status arrays alternate between passes: this pass reads
     // and publishes in `tstat`, and clears its own tiles' slots in the other
     // array for the next pass (which starts only after this one finishes).
-    uint32_t *__restrict__ tstat = tstat_base + (size_t)(pass & 1) * tstride;
-    uint32_t *__restrict__ tnext = tstat_base + (size_t)((pass + 1) & 1) * tstride;
     constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
     if (ctl->key64 != want64 || (uint32_t)pass >= ctl->npasses) return;
+    const uint32_t par = ctl->parity;
+    uint32_t *__restrict__ tstat = tstat_base + (size_t)((pass + par) & 1) * tstride;
+    uint32_t *__restrict__ tnext = tstat_base + (size_t)((pass + par + 1) & 1) * tstride;
     const uint32_t n = ctl->n;
     const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
     const int shift = pass * kRadixBits;
@@ -244,10 +245,12 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
     grid *= per_sm;
     const int tiles = (int)(((uint64_t)max_n + kSortTile - 1) / kSortTile);
     if (grid > tiles) grid = tiles > 0 ? tiles : 1;  // a small sort needs fewer blocks
+    // The look-back array the first pass uses is clear on entry: the key
+    // kernel clears array 0 before the main sort, and every pass clears its
+    // tiles' slots in the other array for the next pass, so after the main
+    // sort the array its pass count points at is clear for the kept sort.
     const size_t tstride = sort_status_words(max_n) / 2;
-    cudaError_t e = cudaMemsetAsync(tile_status, 0, tstride * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    FEC_MARK(ws, "memset_sort_status", st);
+    cudaError_t e = cudaSuccess;
     KeyT *kin = (KeyT *)ka_, *kout = (KeyT *)kb_;
     ValT *vin = (ValT *)va_, *vout = (ValT *)vb_;
     for (int p = 0; p < max_passes; ++p) {

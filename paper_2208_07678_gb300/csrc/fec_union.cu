@@ -298,8 +298,13 @@ __global__ void __launch_bounds__(256, 4)
            const uint32_t *__restrict__ cell_sc, const uint32_t *__restrict__ slab_lo,
            const uint32_t *__restrict__ slab_hi, const uint32_t *__restrict__ col_lo,
            const uint32_t *__restrict__ col_hi, const uint8_t *__restrict__ cocc,
-           uint32_t *__restrict__ nb_first, uint8_t *__restrict__ nb_cnt)
+           uint32_t *__restrict__ nb_first, uint8_t *__restrict__ nb_cnt,
+           unsigned long long *__restrict__ edge_set, uint32_t edge_set_size)
 {
+    // the boundary-edge hash set of k_edges starts empty
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < edge_set_size;
+         i += gridDim.x * blockDim.x)
+        edge_set[i] = ~0ull;
     const uint32_t M = plan->M_c;
     const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
     const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
@@ -367,7 +372,7 @@ struct RegionSmem {
     uint16_t par[kRegionSubs];             // union-find parent, region-local (< 2^16)
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
-    uint32_t ecount, qcount, next, region, pad[4];
+    uint32_t ecount, qcount, next, region, rend, pad[3];
     // per cell slot (two per warp, one per half-warp):
     uint32_t nbl[2 * kRegionWarps][16];    // per neighbour cell: first sub-cell
     uint32_t pre[2 * kRegionWarps][16];    //   its first ordinal among the neighbour sub-cells
@@ -450,10 +455,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     extern __shared__ __align__(16) unsigned char region_smem[];
     RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
     const uint32_t M = plan->M_c;
-    // region size: kRegionCells, or fewer cells when the cloud has too few
-    // cells to give every block two regions
-    const uint32_t rc = min((uint32_t)kRegionCells, max(kRegionMinCells, M / (2u * gridDim.x)));
-    const uint32_t nregions = (M + rc - 1) / rc;
+
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     uint32_t *status = &plan->status;
     Metric<WIDE> m;
@@ -473,11 +475,19 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     auto pair_overflow = [&](uint2) { atomicOr(status, ST_QUEUE_OVERFLOW); };
 
     for (;;) {
-        if (tid == 0) S.region = atomicAdd(&plan->region_counter, 1u);
+        if (tid == 0) {
+            // region size: kRegionCells, or fewer cells when the cloud has too
+            // few cells to give every block two regions
+            const uint32_t rc =
+                min((uint32_t)kRegionCells, max(kRegionMinCells, M / (2u * gridDim.x)));
+            const uint32_t r = atomicAdd(&plan->region_counter, 1u);
+            const uint64_t lo = (uint64_t)r * rc;
+            S.region = lo < M ? (uint32_t)lo : M;
+            S.rend = lo < M ? min((uint32_t)lo + rc, M) : M;
+        }
         __syncthreads();
-        const uint32_t r = S.region;
-        if (r >= nregions) break;
-        const uint32_t c_lo = r * rc, c_hi = min(c_lo + rc, M);
+        const uint32_t c_lo = S.region, c_hi = S.rend;
+        if (c_lo >= M) break;
         const uint32_t s0 = cell_sc[c_lo], s1 = cell_sc[c_hi], ns = s1 - s0;
         for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = (uint16_t)i;
         for (int i = tid; i < kRegionBuf; i += blockDim.x) {
@@ -1007,7 +1017,8 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     }
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item (cell, sub-cell, edge) per thread
     k_nbrs<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
-                                        ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt);
+                                        ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt,
+                                        ws.edge_set, (uint32_t)ws.edge_set_size);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
     const uint32_t scap = region_scratch(ws, ws.cap_n);
@@ -1020,9 +1031,6 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
-    cudaError_t e = cudaMemsetAsync(ws.edge_set, 0xff, sizeof(unsigned long long) * ws.edge_set_size, st);
-    if (e != cudaSuccess) return e;
-    FEC_MARK(ws, "memset_edge_set", st);
     k_edges<<<grid1, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
                                         (uint32_t)(ws.edge_set_size - 1));
     FEC_MARK(ws, "k_edges", st);
