@@ -140,6 +140,14 @@ fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, 
  * request's final error and releases the ticket.  Thread-safe. */
 fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, int timeout_ms);
 
+/* Serving: fec_serve_poll that also reports when the request completed:
+ * *done_ns (if not NULL) is the CLOCK_MONOTONIC time, in nanoseconds, at
+ * which its labels and cluster count were final in host memory (set with
+ * FEC_OK and with a final error).  Lets a caller measure submit-to-completion
+ * latency independently of how often it polls.  Thread-safe. */
+fec_status fec_serve_poll_timed(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters,
+                                int timeout_ms, int64_t *done_ns);
+
 /* Counters of the last fec_cluster / fec_cluster_batch call on ctx. */
 fec_status fec_get_stats(const fec_ctx *ctx, fec_stats *out);
 

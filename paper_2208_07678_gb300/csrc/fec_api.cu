@@ -349,14 +349,16 @@ fec_status ensure_workspace(fec_ctx *ctx, size_t n, uint32_t slab_cap, bool forc
         bytes = workspace_layout(probe, nullptr, cap, sc);
         if (bytes > ctx->budget) return FEC_ERR_OOM;
     }
+    // Stream-ordered: the old workspace is released and the new one taken on
+    // the context's stream, so growing it stalls no other stream (a plain
+    // free would synchronise the whole device).
     if (ws.base) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(ws.base);
+        cudaFreeAsync(ws.base, ctx->stream);
         ws.base = nullptr;
         ws.cap_n = 0;
     }
     void *base = nullptr;
-    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&base, bytes, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         return FEC_ERR_OOM;
     }
@@ -454,6 +456,7 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int6
 }
 
 size_t ctx_budget(const fec_ctx *ctx) { return ctx->budget; }
+cudaStream_t ctx_stream(const fec_ctx *ctx) { return ctx->stream; }
 ServeEngine *ctx_serve(fec_ctx *ctx) { return ctx->serve; }
 
 }  // namespace fec
@@ -510,6 +513,15 @@ fec_status fec_create(const fec_options *opt, fec_ctx **out)
     }
     ctx->ws.device = ctx->device;
     ctx->ws.sms = sm_count();
+    {
+        // keep freed workspaces in the device's stream-ordered pool for reuse
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     if (cudaMalloc(&ctx->summary_dev, sizeof(Summary)) != cudaSuccess ||
         cudaMallocHost(&ctx->summary_host, sizeof(Summary)) != cudaSuccess) {
         cudaGetLastError();
@@ -529,8 +541,8 @@ void fec_destroy(fec_ctx *ctx)
     if (ctx->serve) serve_destroy(ctx->serve);
     if (ctx->batch) batch_destroy(ctx->batch);
     ctx->trace.destroy();
+    if (ctx->ws.base && ctx->stream) cudaFreeAsync(ctx->ws.base, ctx->stream);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->summary_dev) cudaFree(ctx->summary_dev);
     if (ctx->summary_host) cudaFreeHost(ctx->summary_host);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

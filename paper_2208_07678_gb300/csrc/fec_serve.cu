@@ -1,7 +1,8 @@
 // fec_serve.cu -- request loop with continuous batching.
 //
 // Requests (clouds of any size, each with its own d and size bounds) are
-// copied into pinned staging at submit time and queued.  A fixed set of
+// copied to device memory at submit time, on the engine's copy stream, and
+// queued.  A fixed set of
 // worker slots, each with its own CUDA stream and device workspace, takes
 // requests as they arrive: a request is admitted when a slot is free and the
 // sum of the workspace estimates of running requests stays within the memory
@@ -13,6 +14,7 @@
 // Latency of a request = submit -> completion (labels and count in host
 // memory); poll only observes it.
 #include <chrono>
+#include <ctime>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
@@ -29,6 +31,8 @@
 
 namespace fec {
 
+cudaStream_t ctx_stream(const fec_ctx *ctx);  // fec_api.cu
+
 namespace {
 
 constexpr int kSlots = 4;
@@ -36,8 +40,8 @@ constexpr size_t kDefaultBudget = (size_t)40 << 30;  // 40 GiB when the context 
 
 struct Request {
     uint64_t ticket = 0;
-    float *xyz = nullptr;   // pinned copy of the input (from the engine's pool)
-    size_t xyz_cap = 0;
+    float *xyz = nullptr;   // device copy of the input (stream-ordered allocation)
+    cudaEvent_t ready = nullptr;  // the copy has landed
     int64_t n = 0;
     float d = 0;
     int64_t min_size = 0, max_size = 0;
@@ -46,48 +50,14 @@ struct Request {
     fec_status status = FEC_ERR_NOT_READY;
     int32_t k = 0;
     bool done = false;
+    int64_t done_ns = 0;    // CLOCK_MONOTONIC at completion
 };
 
 }  // namespace
 
-// Pinned host buffers reused across requests: allocating and freeing pinned
-// memory per request would serialise the device (freeing pinned memory
-// synchronises it).  Buffers come in power-of-two size classes.
-struct PinnedPool {
-    std::vector<std::pair<size_t, void *>> free_list;  // (capacity, pointer)
-    size_t held = 0;
-
-    void *get(size_t bytes, size_t &cap)
-    {
-        size_t c = 4096;
-        while (c < bytes) c <<= 1;
-        for (size_t i = 0; i < free_list.size(); ++i)
-            if (free_list[i].first == c) {
-                void *p = free_list[i].second;
-                free_list.erase(free_list.begin() + i);
-                cap = c;
-                return p;
-            }
-        void *p = nullptr;
-        if (cudaMallocHost(&p, c) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        held += c;
-        cap = c;
-        return p;
-    }
-    void put(void *p, size_t cap) { free_list.emplace_back(cap, p); }
-    void release_all()
-    {
-        for (auto &e : free_list) cudaFreeHost(e.second);
-        free_list.clear();
-    }
-};
-
 struct ServeEngine {
     fec_ctx *owner = nullptr;
-    PinnedPool pool;
+    cudaStream_t copy = nullptr;  // host -> device copies of submitted inputs
     int device = 0;
     size_t budget = 0;
     size_t in_flight = 0;
@@ -147,16 +117,21 @@ void ServeEngine::worker(int slot)
             in_flight += r->est;
         }
         int32_t k = 0;
+        const cudaStream_t st = ctx_stream(ctx);
+        if (r->ready) cudaStreamWaitEvent(st, r->ready, 0);
         fec_status s = fec_cluster(ctx, r->xyz, r->n, r->d, r->min_size, r->max_size,
                                    r->labels_out, &k);
+        timespec ts;
+        clock_gettime(CLOCK_MONOTONIC, &ts);
+        if (r->xyz) cudaFreeAsync(r->xyz, st);
+        r->xyz = nullptr;
         {
             std::lock_guard<std::mutex> lk(mu);
             in_flight -= r->est;
             r->status = s;
             r->k = k;
+            r->done_ns = (int64_t)ts.tv_sec * 1000000000LL + ts.tv_nsec;
             r->done = true;
-            if (r->xyz) pool.put(r->xyz, r->xyz_cap);
-            r->xyz = nullptr;
         }
         cv_done.notify_all();
         cv_work.notify_all();
@@ -168,6 +143,10 @@ ServeEngine *serve_create(fec_ctx *owner, const char *)
     ServeEngine *e = new ServeEngine();
     e->owner = owner;
     cudaGetDevice(&e->device);
+    if (cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        e->copy = nullptr;
+    }
     return e;
 }
 
@@ -180,12 +159,14 @@ void serve_destroy(ServeEngine *e)
     }
     e->cv_work.notify_all();
     for (auto &t : e->workers) t.join();
+    if (e->copy) cudaStreamSynchronize(e->copy);
     for (auto &kv : e->all) {
-        if (kv.second->xyz) e->pool.put(kv.second->xyz, kv.second->xyz_cap);
+        if (kv.second->xyz) cudaFree(kv.second->xyz);
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
         delete kv.second;
     }
     for (fec_ctx *c : e->slots) fec_destroy(c);
-    e->pool.release_all();
+    if (e->copy) cudaStreamDestroy(e->copy);
     delete e;
 }
 
@@ -197,6 +178,7 @@ using namespace fec;
 // accessors (fec_ctx is defined in fec_api.cu).
 namespace fec {
 size_t ctx_budget(const fec_ctx *ctx);
+cudaStream_t ctx_stream(const fec_ctx *ctx);
 ServeEngine *ctx_serve(fec_ctx *ctx);
 }  // namespace fec
 
@@ -231,15 +213,22 @@ fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, 
         return FEC_ERR_BUSY;
     }
     if (n > 0) {
-        {
-            std::lock_guard<std::mutex> lk(e->mu);
-            r->xyz = (float *)e->pool.get((size_t)n * 12, r->xyz_cap);
-        }
-        if (!r->xyz) {
+        // Copy the input to the device now (the caller may reuse its buffer
+        // once submit returns: a copy from pageable memory returns after the
+        // driver has staged it); the request's slot waits for the event.
+        if (!e->copy || cudaMallocAsync(&r->xyz, (size_t)n * 12, e->copy) != cudaSuccess) {
+            cudaGetLastError();
             delete r;
             return FEC_ERR_OOM;
         }
-        std::memcpy(r->xyz, xyz, (size_t)n * 12);
+        if (cudaMemcpyAsync(r->xyz, xyz, (size_t)n * 12, cudaMemcpyDefault, e->copy) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(r->ready, e->copy) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeAsync(r->xyz, e->copy);
+            delete r;
+            return FEC_ERR_CUDA;
+        }
     }
     {
         std::lock_guard<std::mutex> lk(e->mu);
@@ -254,6 +243,12 @@ fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, 
 }
 
 fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, int timeout_ms)
+{
+    return fec_serve_poll_timed(ctx, ticket, num_clusters, timeout_ms, nullptr);
+}
+
+fec_status fec_serve_poll_timed(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters,
+                                int timeout_ms, int64_t *done_ns)
 {
     if (!ctx) return FEC_ERR_INVALID_ARG;
     ServeEngine *e = ctx_serve(ctx);
@@ -273,7 +268,9 @@ fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, 
     }
     const fec_status s = r->status;
     if (num_clusters) *num_clusters = r->k;
+    if (done_ns) *done_ns = r->done_ns;
     e->all.erase(it);
+    if (r->ready) cudaEventDestroy(r->ready);
     delete r;
     return s;
 }

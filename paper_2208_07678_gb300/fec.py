@@ -28,7 +28,7 @@ FEC_OK, FEC_ERR_NOT_READY, FEC_ERR_TIMEOUT = 0, 7, 9
 
 # Every function the header declares (checked by the CPU tests against include/fec.h).
 EXPORTS = ("fec_create", "fec_destroy", "fec_cluster", "fec_cluster_batch", "fec_serve_submit",
-           "fec_serve_poll", "fec_get_stats", "fec_workspace_bytes", "fec_status_string",
+           "fec_serve_poll", "fec_serve_poll_timed", "fec_get_stats", "fec_workspace_bytes", "fec_status_string",
            "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc")
 FEC_NOALLOC_MAX_POINTS = 32768
 
@@ -93,6 +93,9 @@ def load(build_if_missing: bool = False):
     lib.fec_serve_submit.restype = ctypes.c_int
     lib.fec_serve_poll.argtypes = [vp, ctypes.c_uint64, i32p, ctypes.c_int]
     lib.fec_serve_poll.restype = ctypes.c_int
+    lib.fec_serve_poll_timed.argtypes = [vp, ctypes.c_uint64, i32p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int64)]
+    lib.fec_serve_poll_timed.restype = ctypes.c_int
     lib.fec_get_stats.argtypes = [vp, ctypes.POINTER(fec_stats)]
     lib.fec_get_stats.restype = ctypes.c_int
     lib.fec_workspace_bytes.argtypes = [i64, ctypes.c_float]
@@ -162,6 +165,15 @@ def fec_serve_poll(ctx, ticket, timeout_ms=-1) -> tuple[int, int]:
     k = ctypes.c_int32(-1)
     st = load().fec_serve_poll(ctx, int(ticket), ctypes.byref(k), int(timeout_ms))
     return st, k.value
+
+
+def fec_serve_poll_timed(ctx, ticket, timeout_ms=-1) -> tuple[int, int, int]:
+    """(status, k, done_ns): done_ns is the CLOCK_MONOTONIC completion time."""
+    k = ctypes.c_int32(-1)
+    t = ctypes.c_int64(0)
+    st = load().fec_serve_poll_timed(ctx, int(ticket), ctypes.byref(k), int(timeout_ms),
+                                     ctypes.byref(t))
+    return st, k.value, t.value
 
 
 def fec_get_stats(ctx) -> dict:
@@ -286,6 +298,10 @@ class Context:
     def poll(self, ticket, timeout_ms=-1):
         """(status, k).  Status FEC_OK, or NOT_READY / TIMEOUT while running."""
         return fec_serve_poll(self.handle, ticket, timeout_ms)
+
+    def poll_timed(self, ticket, timeout_ms=-1):
+        """(status, k, done_ns): done_ns = CLOCK_MONOTONIC completion time."""
+        return fec_serve_poll_timed(self.handle, ticket, timeout_ms)
 
     def stats(self) -> dict:
         return fec_get_stats(self.handle)

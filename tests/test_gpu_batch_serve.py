@@ -107,6 +107,28 @@ def test_serve_poll_semantics():
         assert fec.STATUS[st] == "FEC_ERR_INVALID_ARG"
 
 
+def test_serve_completion_time():
+    """poll_timed reports when the request's result was final, on the clock
+    of time.perf_counter (CLOCK_MONOTONIC): after the submit started and
+    before the poll returned; the input buffer may change right after submit."""
+    import time
+
+    with fec.Context(device=0) as srv, fec.Context(device=0) as solo:
+        r = synth.serve_request(5, 4, lo=100_000, hi=120_000)
+        xyz = r.xyz.copy()
+        out = np.zeros(r.n, np.int32)
+        t_submit = time.perf_counter()
+        t = srv.submit(xyz, r.d, r.min_size, r.max_size, out)
+        xyz[:] = 0.0  # the engine copied the input before submit returned
+        st, k, done_ns = srv.poll_timed(t, -1)
+        t_after = time.perf_counter()
+        assert st == fec.FEC_OK
+        assert t_submit <= done_ns * 1e-9 <= t_after
+        want, k_want = solo.cluster(r.xyz, r.d, r.min_size, r.max_size)
+        assert k == k_want
+        np.testing.assert_array_equal(out, want)
+
+
 def test_serve_rejects_over_budget():
     with fec.Context(device=0, mem_budget_bytes=1 << 20) as srv:
         xyz = np.zeros((100_000, 3), np.float32)
