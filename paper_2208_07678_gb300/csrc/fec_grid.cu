@@ -51,9 +51,7 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->n_big = 0;
         plan->n_huge = 0;
         plan->scan_tile_counter = 0;
-        plan->union_counter = 0;
         plan->pairq_n = 0;
-        plan->local_counter = 0;
         plan->use_cols = 0;
         plan->edges_n = 0;
         plan->region_counter = 0;

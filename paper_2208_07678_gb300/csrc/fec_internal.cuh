@@ -8,7 +8,8 @@
 //   a1  grid keys (cell of side S=2h, sub-cell bits)    k_keys (+ radix digit histograms)
 //   a2  LSD radix sort of (key, index), onesweep        k_onesweep (per 8-bit digit)
 //   a3  cell table: sub-cell/cell heads, scan, gather   k_cells, k_subcell_stats, k_slabs
-//   a4  neighbour test + union (27-cell stencil)        k_union
+//   a4  neighbour lists, neighbour test + union         k_nbrs, k_region, k_edges, k_pairs
+//       (27-cell stencil, region-local union-find)
 //   a5  flatten + component statistics                  k_flatten_stats
 //   a6  size filter, order by smallest index, labels    k_kept, sort, k_rank, k_labels
 //
@@ -104,9 +105,7 @@ struct Plan {
     uint32_t n_big;            // sub-cells with more than kBigSubcell points (up to kHugeSubcell)
     uint32_t n_huge;           // sub-cells with more than kHugeSubcell points
     uint32_t scan_tile_counter;
-    uint32_t union_counter;     // dynamic cell chunks of the union step
     uint32_t pairq_n;           // pairs queued for point-level tests
-    uint32_t local_counter;     // dynamic cell chunks of the in-cell step
     uint32_t use_cols;          // 1: the dense column index covers the grid
     uint32_t edges_n;           // boundary edges emitted by the neighbour step
     uint32_t region_counter;    // dynamic regions of the neighbour step
