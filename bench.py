@@ -105,9 +105,12 @@ def ncu_traffic(kernel, workload):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms with
+    timestamps from before the warm-up on; summary() keeps the samples
+    inside the timed windows that were marked (all samples when none fell
+    inside, which it says)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -115,6 +118,7 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.windows = []
 
     def __enter__(self):
         try:
@@ -123,7 +127,8 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}",
                                           f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # nvidia-smi up and sampling before the first timed step
         except Exception:
             self.proc = None
         return self
@@ -137,18 +142,31 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
+    def mark(self, t0, t1):
+        """A timed window, in time.time() seconds."""
+        self.windows.append((t0, t1))
+
     def summary(self):
+        import datetime
+
         if not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append((ts, parts[1:]))
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        inside = [r for ts, r in rows
+                  if ts is not None and any(t0 - 0.01 <= ts <= t1 + 0.01 for t0, t1 in self.windows)]
+        use = inside if inside else [r for _, r in rows]
 
         def num(v):
             try:
@@ -156,12 +174,13 @@ class ClockSampler:
             except ValueError:
                 return None
 
-        sm = [num(r[1]) for r in rows if num(r[1])]
-        mx = [num(r[2]) for r in rows if num(r[2])]
+        sm = [num(r[1]) for r in use if num(r[1])]
+        mx = [num(r[2]) for r in use if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in use for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(use),
+                "window": "timed steps" if inside else "whole measurement (no sample inside the timed steps)"}
 
 
 def make_workload(name):
@@ -481,23 +500,26 @@ def run_ours(args):
     def step_e2e():
         return ctx.cluster(xyz_host, cloud.d, cloud.min_size, cloud.max_size, labels=lab_host)[1]
 
-    def timed(fn, steps):
+    def timed(fn, steps, clocks=None):
         barrier(world)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
         e0.record(stream)
         for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        if clocks is not None:
+            clocks.mark(w0, time.time())
         barrier(world)
         return e0.elapsed_time(e1) / steps
 
-    for _ in range(args.warmup):
-        k = step_dev()
     with ClockSampler(local) as clocks:
-        ms_dev = timed(step_dev, args.steps)
+        for _ in range(args.warmup):
+            k = step_dev()
+        ms_dev = timed(step_dev, args.steps, clocks)
         # traced pass: per-kernel device time with CUDA events on the same stream
         ctx.trace(True)
         ms_traced = timed(step_dev, args.steps)
@@ -505,7 +527,7 @@ def run_ours(args):
         ctx.trace(False)
         for _ in range(max(1, args.warmup // 2)):
             step_e2e()
-        ms_e2e = timed(step_e2e, args.steps)
+        ms_e2e = timed(step_e2e, args.steps, clocks)
     clk = clocks.summary()
     stats = ctx.stats()
     ms_dev_max = max_over_ranks(ms_dev, world, dev)

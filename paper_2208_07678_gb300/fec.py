@@ -4,7 +4,7 @@ Argument marshalling only: every step of the clustering runs in the CUDA
 library.  There is no CPU fallback; if the library is missing this module
 raises on first use.  Functions keep the C names (``fec_create``,
 ``fec_cluster``, ``fec_cluster_batch``, ``fec_serve_submit``,
-``fec_serve_poll``, ``fec_get_stats``, ``fec_workspace_bytes``,
+``fec_serve_poll``, ``fec_serve_poll_timed``, ``fec_get_stats``, ``fec_workspace_bytes``,
 ``fec_status_string``, ``fec_destroy``) and take raw pointers like the C ABI;
 ``Context`` adds array conveniences on top (numpy arrays = host memory,
 torch CUDA tensors = device memory).
