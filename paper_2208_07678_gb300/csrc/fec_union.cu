@@ -937,18 +937,27 @@ __global__ void __launch_bounds__(256)
 }
 
 // a6: the label of every sub-cell (its root's rank, or -1), written over the
-// component-size array, which is not needed after k_kept.
+// component-size array, which is not needed after k_kept; and every label of
+// the output set to -1 (coalesced), so that k_labels writes kept points only.
 __global__ void __launch_bounds__(256)
     k_sclabel(Plan *plan, const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
-              int32_t *__restrict__ sclab)
+              int32_t *__restrict__ sclab, int32_t *__restrict__ labels, uint32_t n)
 {
     const uint32_t M = plan->M_s;
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x)
         sclab[a] = crank[parent[a]];
+    // 16-byte stores when the output is 16-byte aligned (a batch frame's
+    // labels start anywhere), else 4-byte stores
+    const uint32_t n4 = (reinterpret_cast<uintptr_t>(labels) & 15) ? 0u : n / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x)
+        __stcs(reinterpret_cast<int4 *>(labels) + q, make_int4(-1, -1, -1, -1));
+    for (uint32_t i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        labels[i] = -1;
 }
 
-// a6: labels in input order, eight sorted positions per thread and step
-// (all loads of a step issued before their results are used).
+// a6: labels of the kept points in input order (the others are already -1),
+// eight sorted positions per thread and step; a step whose eight points all
+// belong to dropped components reads no indices.
 __global__ void __launch_bounds__(256)
     k_labels(Plan *plan, const uint32_t *__restrict__ idx_a, const uint32_t *__restrict__ idx_b,
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
@@ -959,6 +968,22 @@ __global__ void __launch_bounds__(256)
     const uint32_t n8 = n / 8;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += gridDim.x * blockDim.x) {
         uint32_t i[8], sc[8];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(sc_of) + 2 * (size_t)q + t);
+            sc[4 * t] = v.x;
+            sc[4 * t + 1] = v.y;
+            sc[4 * t + 2] = v.z;
+            sc[4 * t + 3] = v.w;
+        }
+        int32_t l[8];
+        bool any = false;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            l[t] = sclab[sc[t]];
+            any |= l[t] >= 0;
+        }
+        if (!any) continue;
         if (idx_stride == 2) {
             const uint4 *src = reinterpret_cast<const uint4 *>(idx) + 4 * (size_t)q;
 #pragma unroll
@@ -979,24 +1004,14 @@ __global__ void __launch_bounds__(256)
             }
         }
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(sc_of) + 2 * (size_t)q + t);
-            sc[4 * t] = v.x;
-            sc[4 * t + 1] = v.y;
-            sc[4 * t + 2] = v.z;
-            sc[4 * t + 3] = v.w;
-        }
-        int32_t l[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) l[t] = sclab[sc[t]];
-#pragma unroll
         for (int t = 0; t < 8; ++t)
-            if (i[t] < n) labels[i[t]] = l[t];
+            if (l[t] >= 0 && i[t] < n) labels[i[t]] = l[t];
     }
     for (uint32_t p = n8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += gridDim.x * blockDim.x) {
+        const int32_t l = sclab[sc_of[p]];
         const uint32_t i = idx[(size_t)p * idx_stride];
-        if (i < n) labels[i] = sclab[sc_of[p]];
+        if (l >= 0 && i < n) labels[i] = l;
     }
 }
 
@@ -1058,7 +1073,7 @@ cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bo
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
     int32_t *sclab = (int32_t *)ws.csize;  // component sizes are no longer needed
-    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab);
+    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab, labels, prm.n);
     FEC_MARK(ws, "k_sclabel", st);
     k_labels<<<grid_for(ws, prm.n, 2048, 8), 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
                                          (const uint32_t *)ws.vals_b, packed ? 2u : 1u, ws.sc_of,
