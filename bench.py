@@ -52,7 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 #                    sub-cell label 4 per sub-cell
 KERNEL_BYTES = {
     "k_bbox": lambda n, Ms, Mc: 12 * n,
-    "k_keys": lambda n, Ms, Mc: 24 * n,
+    "k_keys": lambda n, Ms, Mc: 12 * n,   # packed layout: histograms only, the sort's first pass makes the keys
     "onesweep_u32": lambda n, Ms, Mc: 24 * n,
     "k_cells": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
     "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 72 * Ms,

@@ -159,13 +159,14 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
     // a2: both key widths are enqueued; the plan enables one of them.
     const bool pk = prm.packed != 0;
     e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b, ws.vals_b,
-                    false, pk, !pk, ws.sort_status, n, 4, sort_grid, st, &ws.plan->status);
+                    false, pk, !pk, ws.sort_status, n, 4, sort_grid, st, &ws.plan->status,
+                    main_sort_source(ws, xyz, prm));
     if (e != cudaSuccess) return e;
     const int p64 = max_sort_passes(prm);
     if (p64 > 4) {
         e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
                         ws.vals_b, true, pk, !pk, ws.sort_status, n, p64, sort_grid, st,
-                        &ws.plan->status);
+                        &ws.plan->status, main_sort_source(ws, xyz, prm));
         if (e != cudaSuccess) return e;
     }
     e = enqueue_cells(ws, xyz, prm, st);

@@ -194,84 +194,6 @@ __global__ void k_plan(Plan *plan, Params prm)
     plan->kept.parity = plan->sort.npasses & 1u;  // the look-back array the main sort leaves clear
 }
 
-// Element i (0..2) of a 3-vector held in registers (no local-memory indexing).
-template <typename T>
-__device__ __forceinline__ T sel3(const T v[3], int i)
-{
-    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
-}
-
-// Grid coordinates of a quantised point under the plan.
-struct GridMap {
-    int32_t lo[3];
-    int perm[3];
-    uint32_t bits[3];
-    int32_t S, h;
-    uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
-
-    __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
-    {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = plan->lo[a];
-            perm[a] = plan->perm[a];
-            bits[a] = plan->bits[a];
-        }
-        S = prm.S;
-        h = prm.h;
-        div_m = prm.div_m;
-        div_s = prm.div_s;
-    }
-    // Cell coordinate and offset inside the cell, per original axis.
-    __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
-    {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const uint32_t rel = (uint32_t)(q[a] - lo[a]);
-            c[a] = (uint32_t)(((unsigned long long)rel * div_m) >> div_s);
-            off[a] = rel - c[a] * (uint32_t)S;
-        }
-    }
-    // Sort key: [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2], c = cell coordinate,
-    // s = which half of the cell (sub-cell bit).
-    __device__ __forceinline__ unsigned long long key_of(const uint32_t c[3], const uint32_t off[3]) const
-    {
-        unsigned long long k = 0;
-        uint32_t sub = 0;
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            k = (k << bits[p]) | sel3(c, perm[p]);
-            sub = (sub << 1) | (sel3(off, perm[p]) >= (uint32_t)h ? 1u : 0u);
-        }
-        return (k << 3) | sub;
-    }
-    // Sort payload of the packed layout: the original index in the low 32
-    // bits and the point's offsets inside its cell (original axes x, y, z,
-    // 10 bits each, S <= 1024) above it.
-    __device__ __forceinline__ unsigned long long payload_of(const uint32_t off[3], uint32_t idx) const
-    {
-        return (unsigned long long)idx | ((unsigned long long)off[0] << 32) |
-               ((unsigned long long)off[1] << 42) | ((unsigned long long)off[2] << 52);
-    }
-    // Inverse of key_of() + payload_of(): the quantised coordinates of a point.
-    __device__ __forceinline__ void unpack(unsigned long long key, unsigned long long v,
-                                           int32_t q[3]) const
-    {
-        unsigned long long ck = key >> 3;
-        uint32_t cp[3];
-#pragma unroll
-        for (int p = 2; p >= 0; --p) {
-            cp[p] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
-            ck >>= bits[p];
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const uint32_t c = perm[0] == a ? cp[0] : (perm[1] == a ? cp[1] : cp[2]);
-            q[a] = lo[a] + (int32_t)(c * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
-        }
-    }
-};
-
 // Arrays zeroed by the key kernel for the later stages.
 struct Clears {
     uint32_t *sort_status;          // look-back array 0 of the main sort
@@ -284,7 +206,10 @@ struct Clears {
 };
 
 // a1: grid keys of all points, plus the digit histograms of every radix pass.
-template <typename KeyT, bool PACKED>
+// With STORE false only the histograms are made: the sort's first pass then
+// computes the keys and payloads again from the coordinates it reads, which
+// saves writing and re-reading them (packed layout only).
+template <typename KeyT, bool PACKED, bool STORE>
 __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *plan, const Params &prm,
                                           KeyT *__restrict__ keys,
                                           unsigned long long *__restrict__ vals, const Clears &clr,
@@ -344,7 +269,8 @@ __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *p
             k[u] = (KeyT)g.key_of(c, off);
             v[u] = g.payload_of(off, i0 + u);
         }
-        if (cnt == 4) {
+        if (!STORE) {
+        } else if (cnt == 4) {
             if (sizeof(KeyT) == 4) {
                 reinterpret_cast<uint4 *>(keys)[gi] =
                     make_uint4((uint32_t)k[0], (uint32_t)k[1], (uint32_t)k[2], (uint32_t)k[3]);
@@ -377,16 +303,17 @@ __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *p
 }
 
 // The key kernel for either key width (the plan selects it on the device).
-template <bool PACKED>
+template <bool PACKED, bool STORE>
 __global__ void __launch_bounds__(256)
     k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, void *__restrict__ keys,
            unsigned long long *__restrict__ vals, Clears clr)
 {
     __shared__ uint32_t h[kMaxPasses][kRadixBins];
     if (plan->sort.key64)
-        keys_body<unsigned long long, PACKED>(xyz, plan, prm, (unsigned long long *)keys, vals, clr, h);
+        keys_body<unsigned long long, PACKED, STORE>(xyz, plan, prm, (unsigned long long *)keys, vals,
+                                                     clr, h);
     else
-        keys_body<uint32_t, PACKED>(xyz, plan, prm, (uint32_t *)keys, vals, clr, h);
+        keys_body<uint32_t, PACKED, STORE>(xyz, plan, prm, (uint32_t *)keys, vals, clr, h);
 }
 
 // a3: cell table from the sorted keys, in one pass with a decoupled look-back
@@ -457,6 +384,21 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
 #pragma unroll
                 for (int t = 0; t < per; ++t) k[v * per + t] = e[t];
             }
+        }
+        // the payloads too, so that their loads overlap the scan and look-back
+        ValT vv[kScanIPT];
+        if (full) {
+            constexpr int per = 16 / sizeof(ValT);
+#pragma unroll
+            for (int v = 0; v < kScanIPT / per; ++v) {
+                const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(vals + p0) + v);
+                const ValT *e = reinterpret_cast<const ValT *>(&w);
+#pragma unroll
+                for (int t = 0; t < per; ++t) vv[v * per + t] = e[t];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : (ValT)0;
         }
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
@@ -535,20 +477,6 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
         __syncthreads();
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
 
-        ValT vv[kScanIPT];
-        if (full) {
-            constexpr int per = 16 / sizeof(ValT);
-#pragma unroll
-            for (int v = 0; v < kScanIPT / per; ++v) {
-                const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(vals + p0) + v);
-                const ValT *e = reinterpret_cast<const ValT *>(&w);
-#pragma unroll
-                for (int t = 0; t < per; ++t) vv[v * per + t] = e[t];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kScanIPT; ++i) vv[i] = (p0 + i < n) ? vals[p0 + i] : (ValT)0;
-        }
         unsigned long long before = base;
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
@@ -918,10 +846,11 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cu
     clr.slab_words = prm.slab_cap;
     clr.max_words = clr.sort_words > clr.scan_words ? clr.sort_words : clr.scan_words;
     if (clr.slab_words > clr.max_words) clr.max_words = clr.slab_words;
+    // packed layout: the sort's first pass computes the keys itself
     if (prm.packed)
-        k_keys<true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+        k_keys<true, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
     else
-        k_keys<false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+        k_keys<false, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
     FEC_MARK(ws, "k_keys", st);
     return cudaGetLastError();
 }

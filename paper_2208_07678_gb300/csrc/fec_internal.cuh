@@ -54,7 +54,7 @@ constexpr int kMaxPasses = 8;            // 64-bit keys
 #define FEC_SORT_THREADS 512
 #endif
 #ifndef FEC_SORT_IPT
-#define FEC_SORT_IPT 8
+#define FEC_SORT_IPT 10
 #endif
 #ifndef FEC_SORT_MINB
 #define FEC_SORT_MINB 2
@@ -62,7 +62,7 @@ constexpr int kMaxPasses = 8;            // 64-bit keys
 constexpr int kSortThreads = FEC_SORT_THREADS;
 constexpr int kSortIPT = FEC_SORT_IPT;   // items per thread
 constexpr int kSortMinBlocks = FEC_SORT_MINB;
-constexpr int kSortTile = kSortThreads * kSortIPT;   // 4096 keys per tile
+constexpr int kSortTile = kSortThreads * kSortIPT;   // 5120 keys per tile
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
@@ -162,6 +162,84 @@ __device__ __forceinline__ int quantize1(float x, int32_t &q)
     q = __float2int_rn(r);
     return 0;
 }
+
+// Element i (0..2) of a 3-vector held in registers (no local-memory indexing).
+template <typename T>
+__device__ __forceinline__ T sel3(const T v[3], int i)
+{
+    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
+// Grid coordinates of a quantised point under the plan.
+struct GridMap {
+    int32_t lo[3];
+    int perm[3];
+    uint32_t bits[3];
+    int32_t S, h;
+    uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
+
+    __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = plan->lo[a];
+            perm[a] = plan->perm[a];
+            bits[a] = plan->bits[a];
+        }
+        S = prm.S;
+        h = prm.h;
+        div_m = prm.div_m;
+        div_s = prm.div_s;
+    }
+    // Cell coordinate and offset inside the cell, per original axis.
+    __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t rel = (uint32_t)(q[a] - lo[a]);
+            c[a] = (uint32_t)(((unsigned long long)rel * div_m) >> div_s);
+            off[a] = rel - c[a] * (uint32_t)S;
+        }
+    }
+    // Sort key: [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2], c = cell coordinate,
+    // s = which half of the cell (sub-cell bit).
+    __device__ __forceinline__ unsigned long long key_of(const uint32_t c[3], const uint32_t off[3]) const
+    {
+        unsigned long long k = 0;
+        uint32_t sub = 0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            k = (k << bits[p]) | sel3(c, perm[p]);
+            sub = (sub << 1) | (sel3(off, perm[p]) >= (uint32_t)h ? 1u : 0u);
+        }
+        return (k << 3) | sub;
+    }
+    // Sort payload of the packed layout: the original index in the low 32
+    // bits and the point's offsets inside its cell (original axes x, y, z,
+    // 10 bits each, S <= 1024) above it.
+    __device__ __forceinline__ unsigned long long payload_of(const uint32_t off[3], uint32_t idx) const
+    {
+        return (unsigned long long)idx | ((unsigned long long)off[0] << 32) |
+               ((unsigned long long)off[1] << 42) | ((unsigned long long)off[2] << 52);
+    }
+    // Inverse of key_of() + payload_of(): the quantised coordinates of a point.
+    __device__ __forceinline__ void unpack(unsigned long long key, unsigned long long v,
+                                           int32_t q[3]) const
+    {
+        unsigned long long ck = key >> 3;
+        uint32_t cp[3];
+#pragma unroll
+        for (int p = 2; p >= 0; --p) {
+            cp[p] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
+            ck >>= bits[p];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t c = perm[0] == a ? cp[0] : (perm[1] == a ? cp[1] : cp[2]);
+            q[a] = lo[a] + (int32_t)(c * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
+        }
+    }
+};
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
@@ -373,10 +451,31 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
 // Kernels for a key width that ctl->key64 does not select return at once, so
 // both widths can be enqueued blindly.  The result lands in keys_a/vals_a if
 // npasses is even, else in keys_b/vals_b.
+// Where the first pass of a sort gets its keys: from keys_a/vals_a (xyz
+// null), or computed from the coordinates under the plan (packed payloads;
+// the key kernel then only makes the histograms).
+struct SortSource {
+    const float *xyz = nullptr;
+    const Plan *plan = nullptr;
+    Params prm{};
+};
 cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, void *keys_a,
                         void *vals_a, void *keys_b, void *vals_b, bool key64, bool val64,
                         bool identity_vals, uint32_t *tile_status, uint32_t max_n, int max_passes,
-                        int grid, cudaStream_t st, uint32_t *status);
+                        int grid, cudaStream_t st, uint32_t *status,
+                        const SortSource &src = SortSource());
+// The main sort's source, matching enqueue_front (which stores keys only
+// when the payloads are not packed).
+inline SortSource main_sort_source(const Workspace &ws, const float *xyz, const Params &prm)
+{
+    SortSource s;
+    if (prm.packed) {
+        s.xyz = xyz;
+        s.plan = ws.plan;
+        s.prm = prm;
+    }
+    return s;
+}
 // uint32 words of look-back status a sort of up to max_n keys needs.
 inline size_t sort_status_words(uint32_t max_n)
 {

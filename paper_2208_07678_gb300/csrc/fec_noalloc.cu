@@ -110,12 +110,12 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
     if (e == cudaSuccess)
         e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
                         ws.vals_b, false, pk, !pk, ws.sort_status, un, 4, ws.sms, st,
-                        &ws.plan->status);
+                        &ws.plan->status, main_sort_source(ws, xin, prm));
     const int p64 = max_sort_passes(prm);
     if (e == cudaSuccess && p64 > 4)
         e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
                         ws.vals_b, true, pk, !pk, ws.sort_status, un, p64, ws.sms, st,
-                        &ws.plan->status);
+                        &ws.plan->status, main_sort_source(ws, xin, prm));
     if (e == cudaSuccess) e = enqueue_cells(ws, xin, prm, st);
     if (e == cudaSuccess) e = enqueue_union(ws, prm, min_size, max_size, st);
     const int kp = kept_sort_passes(un);

@@ -61,12 +61,16 @@ __device__ __forceinline__ void scan256(const uint32_t *in, uint32_t *out, uint3
     __syncthreads();
 }
 
-template <typename KeyT, typename ValT>
+// XYZ: the first pass of the main sort in the packed layout, which reads the
+// coordinates and computes each point's key and payload itself (the key
+// kernel only made the histograms), instead of reading stored keys.
+template <typename KeyT, typename ValT, bool XYZ>
 __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     k_onesweep(SortCtl *__restrict__ ctl, const KeyT *__restrict__ kin,
                const ValT *__restrict__ vin, KeyT *__restrict__ kout,
                ValT *__restrict__ vout, uint32_t *__restrict__ tstat_base, size_t tstride,
-               int pass, uint32_t *__restrict__ status)
+               int pass, uint32_t *__restrict__ status, const float *__restrict__ xyz,
+               const Plan *__restrict__ plan, Params prm)
 {
     // Two look-back status arrays alternate between passes: this pass reads
     // and publishes in `tstat`, and clears its own tiles' slots in the other
@@ -84,6 +88,8 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     SortSmem<KeyT, ValT> &S = *reinterpret_cast<SortSmem<KeyT, ValT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+    __shared__ GridMap gm;  // read from shared memory: it would cost registers
+    if (XYZ && tid == 0) gm.load(plan, prm);
     if (tid < kRadixBins) S.cnt[tid] = ctl->hist[pass][tid];
     __syncthreads();
     scan256(S.cnt, S.gofs, S.warp_tot);
@@ -100,12 +106,41 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
         ValT val[kSortIPT];
         uint32_t lrank[kSortIPT], dig[kSortIPT];
         const uint32_t seg = tile * (uint32_t)kSortTile + warp * (32u * kSortIPT);
+        // all of the thread's loads first, so that they are in flight together
+        // (the ranking loop below synchronises the warp after every item)
+        if (XYZ) {
+            float f[3 * kSortIPT];
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t pos = seg + r * 32 + lane;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    f[3 * r + a] = pos < n ? __ldcs(xyz + 3 * (size_t)pos + a) : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t pos = seg + r * 32 + lane;
+                int32_t q[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) quantize1(f[3 * r + a], q[a]);
+                uint32_t c[3], off[3];
+                gm.cell_of(q, c, off);
+                key[r] = (KeyT)gm.key_of(c, off);
+                val[r] = (ValT)gm.payload_of(off, pos);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t pos = seg + r * 32 + lane;
+                const bool valid = pos < n;
+                key[r] = valid ? kin[pos] : KeyT(0);
+                val[r] = valid ? (vin ? vin[pos] : (ValT)pos) : (ValT)0;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
             const uint32_t pos = seg + r * 32 + lane;
             const bool valid = pos < n;
-            key[r] = valid ? kin[pos] : KeyT(0);
-            val[r] = valid ? (vin ? vin[pos] : (ValT)pos) : (ValT)0;
             const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRadixBins - 1)
                                      : (uint32_t)kRadixBins + lane;
             dig[r] = d;
@@ -230,17 +265,24 @@ template <typename KeyT, typename ValT>
 cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, void *ka_, void *va_,
                           void *kb_, void *vb_, bool identity_vals, uint32_t *tile_status,
                           uint32_t max_n, int max_passes, int grid, cudaStream_t st,
-                          uint32_t *status)
+                          uint32_t *status, const SortSource &src)
 {
     const size_t smem = sizeof(SortSmem<KeyT, ValT>);
     static int per_sm = 0;  // resident blocks per SM (persistent grid)
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT>,
+        cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<KeyT, ValT>,
+        e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int a = 0, b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_onesweep<KeyT, ValT, false>,
                                                           kSortThreads, smem);
-        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep<KeyT, ValT, true>,
+                                                              kSortThreads, smem);
+        per_sm = (e != cudaSuccess || a < 1 || b < 1) ? 1 : (a < b ? a : b);
     }
     grid *= per_sm;
     const int tiles = (int)(((uint64_t)max_n + kSortTile - 1) / kSortTile);
@@ -254,9 +296,14 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
     KeyT *kin = (KeyT *)ka_, *kout = (KeyT *)kb_;
     ValT *vin = (ValT *)va_, *vout = (ValT *)vb_;
     for (int p = 0; p < max_passes; ++p) {
-        k_onesweep<KeyT, ValT><<<grid, kSortThreads, smem, st>>>(
-            ctl, kin, (p == 0 && identity_vals) ? nullptr : vin, kout, vout, tile_status, tstride,
-            p, status);
+        if (p == 0 && src.xyz)
+            k_onesweep<KeyT, ValT, true><<<grid, kSortThreads, smem, st>>>(
+                ctl, nullptr, nullptr, kout, vout, tile_status, tstride, p, status, src.xyz,
+                src.plan, src.prm);
+        else
+            k_onesweep<KeyT, ValT, false><<<grid, kSortThreads, smem, st>>>(
+                ctl, kin, (p == 0 && identity_vals) ? nullptr : vin, kout, vout, tile_status,
+                tstride, p, status, nullptr, nullptr, src.prm);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         FEC_MARK(ws, name, st);
@@ -275,21 +322,22 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
 cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, void *keys_a,
                         void *vals_a, void *keys_b, void *vals_b, bool key64, bool val64,
                         bool identity_vals, uint32_t *tile_status, uint32_t max_n, int max_passes,
-                        int grid, cudaStream_t st, uint32_t *status)
+                        int grid, cudaStream_t st, uint32_t *status, const SortSource &src)
 {
+    if (src.xyz && !val64) return cudaErrorInvalidValue;  // keys from xyz: packed payloads only
     using u32 = uint32_t;
     using u64 = unsigned long long;
     if (!key64 && !val64)
         return launch_sort_t<u32, u32>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                       tile_status, max_n, max_passes, grid, st, status);
+                                       tile_status, max_n, max_passes, grid, st, status, src);
     if (!key64)
         return launch_sort_t<u32, u64>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                       tile_status, max_n, max_passes, grid, st, status);
+                                       tile_status, max_n, max_passes, grid, st, status, src);
     if (!val64)
         return launch_sort_t<u64, u32>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                       tile_status, max_n, max_passes, grid, st, status);
+                                       tile_status, max_n, max_passes, grid, st, status, src);
     return launch_sort_t<u64, u64>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
-                                   tile_status, max_n, max_passes, grid, st, status);
+                                   tile_status, max_n, max_passes, grid, st, status, src);
 }
 
 cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st)

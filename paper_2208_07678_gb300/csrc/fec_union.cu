@@ -373,12 +373,12 @@ struct RegionSmem {
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
     uint32_t ecount, qcount, next, region, rend, pad[3];
-    // per cell slot (two per warp, one per half-warp):
-    uint32_t nbl[2 * kRegionWarps][16];    // per neighbour cell: first sub-cell
-    uint32_t pre[2 * kRegionWarps][16];    //   its first ordinal among the neighbour sub-cells
-    uint8_t kof[2 * kRegionWarps][112];    // per neighbour sub-cell: its neighbour cell
-    uint8_t nocc[2 * kRegionWarps][16];    // per neighbour cell: sub-cell occupancy
-    uint8_t nmask[2 * kRegionWarps][16];   // per neighbour cell: axes at +1 (bits 0-2), at -1 (3-4)
+    // per cell slot (two per warp, one per half-warp), per neighbour sub-cell
+    // (in stencil order): its index, and its code (bits 0-2) with its cell's
+    // axes at +1 (bits 3-5) and at -1 (bits 6-7); per own sub-cell: its code
+    uint32_t nsub[2 * kRegionWarps][112];
+    uint8_t ninfo[2 * kRegionWarps][112];
+    uint8_t ocode[2 * kRegionWarps][8];
     uint32_t qa[kRegionWarps][64];         // queued pairs (a, b) of each warp
     uint32_t qb[kRegionWarps][64];
 };
@@ -544,12 +544,15 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     }
                     const uint32_t T = __shfl_sync(0xffffffffu, ci, 15, 16);
                     if (hl < K) {
-                        S.nbl[cs][hl] = first;
-                        S.pre[cs][hl] = ci - cnt;
-                        S.nocc[cs][hl] = (uint8_t)occ;
-                        S.nmask[cs][hl] = (uint8_t)((mw >> (8 * (hl & 3))) & 255u);
-                        for (uint32_t j = ci - cnt; j < ci; ++j) S.kof[cs][j] = (uint8_t)hl;
+                        const uint32_t nm = ((mw >> (8 * (hl & 3))) & 31u) << 3;
+                        uint32_t rest = occ;
+                        for (uint32_t j = ci - cnt, b = first; j < ci; ++j, ++b) {
+                            S.nsub[cs][j] = b;
+                            S.ninfo[cs][j] = (uint8_t)(nm | (__ffs(rest) - 1));
+                            rest &= rest - 1;
+                        }
                     }
+                    if ((uint32_t)hl < na) S.ocode[cs][hl] = (uint8_t)select8(own, hl);
                     __syncwarp();
                     P0 = na * (na - 1) / 2;
                     P = P0 + na * T;
@@ -564,29 +567,26 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 uint32_t a = 0, b = 0;
                 if (i < P) {
                     if (i < P0) {
-                        uint32_t rem = i, ia = 0;
-                        while (rem >= na - 1 - ia) {
-                            rem -= na - 1 - ia;
-                            ++ia;
-                        }
-                        a = a_lo + ia;
-                        b = a_lo + ia + 1 + rem;
+                        // own pair i = ib (ib - 1) / 2 + ia, ia < ib < na <= 8
+                        const uint32_t ib = 1u + (i >= 1) + (i >= 3) + (i >= 6) + (i >= 10) +
+                                            (i >= 15) + (i >= 21);
+                        a = a_lo + (i - ib * (ib - 1) / 2);
+                        b = a_lo + ib;
                         possible = true;
                     } else {
                         const uint32_t j = i - P0;
                         const uint32_t jb = (j * rcp) >> 16;
                         const uint32_t ia = j - jb * na;
-                        const uint32_t k = S.kof[cs][jb];
-                        b = S.nbl[cs][k] + (jb - S.pre[cs][k]);
+                        b = S.nsub[cs][jb];
                         a = a_lo + ia;
                         // Sub-cells three sub-cell steps apart on an axis are
                         // more than 2h >= R apart: along an axis where the
                         // neighbour cell is at +1, a in the lower half and b
                         // in the upper half (at -1: the reverse) cannot join.
-                        const uint32_t A = select8(own, ia);
-                        const uint32_t B = select8(S.nocc[cs][k], jb - S.pre[cs][k]);
-                        const uint32_t nm = S.nmask[cs][k];
-                        possible = (((nm & 7u) & ~A & B) | ((nm >> 3) & A & ~B)) == 0;
+                        const uint32_t A = S.ocode[cs][ia];
+                        const uint32_t info = S.ninfo[cs][jb];
+                        const uint32_t B = info & 7u;
+                        possible = ((((info >> 3) & 7u) & ~A & B) | ((info >> 6) & A & ~B)) == 0;
                     }
                 }
                 const uint32_t pm = __ballot_sync(0xffffffffu, possible);
