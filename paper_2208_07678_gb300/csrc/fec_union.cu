@@ -527,6 +527,8 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     a_lo = have ? cell_sc[c] : 0u;
                     // neighbour record (32 bytes): occupancies, offsets, K
                     const uint32_t cw = (have && hl < 8) ? reinterpret_cast<const uint32_t *>(nb_cnt)[(size_t)c * 8 + hl] : 0u;
+                    // loaded with the record, not after it (13 entries per cell below M)
+                    const uint32_t first = (have && hl < 13) ? nb_first[(size_t)c * 13 + hl] : 0u;
                     const uint32_t w3 = __shfl_sync(0xffffffffu, cw, 3, 16);
                     const int K = (int)(w3 >> 24);
                     own = (w3 >> 8) & 255u;
@@ -535,7 +537,6 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     const uint32_t mw = __shfl_sync(0xffffffffu, cw, 4 + ((hl >> 2) & 3), 16);
                     const uint32_t occ = (ow >> (8 * (hl & 3))) & 255u;
                     const uint32_t cnt = hl < K ? (uint32_t)__popc(occ) : 0u;
-                    const uint32_t first = hl < K ? nb_first[(size_t)c * 13 + hl] : 0u;
                     uint32_t ci = cnt;
 #pragma unroll
                     for (int o = 1; o < 16; o <<= 1) {
@@ -608,11 +609,13 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 a = S.qa[w][lane];
                 b = S.qb[w][lane];
                 local = b - s0 < ns;
+                const SubBox BA = box[a], BB = box[b];
+                const Rec RA = reps[a], RB = reps[b];
                 if (local && s_find(vpar, a - s0) == s_find(vpar, b - s0)) {
                     ++n_same;
                 } else {
                     ++n_pairs;
-                    dec = box_decide<WIDE>(box[a], box[b], reps[a], reps[b], m);
+                    dec = box_decide<WIDE>(BA, BB, RA, RB, m);
                 }
             }
             // the rest of the queue (fewer than 32) moves to its front
