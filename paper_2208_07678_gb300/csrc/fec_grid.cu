@@ -266,7 +266,7 @@ __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *p
             for (int a = 0; a < 3; ++a) quantize1(f[3 * u + a], q[a]);
             uint32_t c[3], off[3];
             g.cell_of(q, c, off);
-            k[u] = (KeyT)g.key_of(c, off);
+            k[u] = g.key_of<KeyT>(c, off);
             v[u] = g.payload_of(off, i0 + u);
         }
         if (!STORE) {
@@ -505,7 +505,7 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             Rec r;
             if (PACKED) {
                 int32_t q[3];
-                g.unpack((unsigned long long)k[i], (unsigned long long)vv[i], q);
+                g.unpack<KeyT>(k[i], (unsigned long long)vv[i], q);
                 r.x = q[0];
                 r.y = q[1];
                 r.z = q[2];

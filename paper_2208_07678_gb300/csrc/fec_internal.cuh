@@ -163,28 +163,28 @@ __device__ __forceinline__ int quantize1(float x, int32_t &q)
     return 0;
 }
 
-// Element i (0..2) of a 3-vector held in registers (no local-memory indexing).
-template <typename T>
-__device__ __forceinline__ T sel3(const T v[3], int i)
-{
-    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
-}
-
-// Grid coordinates of a quantised point under the plan.
+// Grid coordinates of a quantised point under the plan.  The sort key is
+// [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2] (c = cell coordinate along the
+// permuted axes, major first; s = which half of the cell), so every original
+// axis a has a fixed place in it: its cell coordinate at bit ksh[a] (kwid[a]
+// bits wide) and its half at bit kbit[a].  These are resolved once in load(), so
+// a point's key is a few shifts with no per-point axis selection.
 struct GridMap {
     int32_t lo[3];
-    int perm[3];
-    uint32_t bits[3];
+    uint32_t ksh[3], kbit[3], kwid[3];
     int32_t S, h;
     uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
 
     __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
     {
+        const uint32_t b0 = plan->bits[0], b1 = plan->bits[1], b2 = plan->bits[2];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a) {  // constant indices only (no local memory)
             lo[a] = plan->lo[a];
-            perm[a] = plan->perm[a];
-            bits[a] = plan->bits[a];
+            const int p = plan->perm[0] == a ? 0 : (plan->perm[1] == a ? 1 : 2);
+            ksh[a] = 3u + (p == 0 ? b1 + b2 : (p == 1 ? b2 : 0u));
+            kbit[a] = 2u - (uint32_t)p;
+            kwid[a] = p == 0 ? b0 : (p == 1 ? b1 : b2);
         }
         S = prm.S;
         h = prm.h;
@@ -201,18 +201,15 @@ struct GridMap {
             off[a] = rel - c[a] * (uint32_t)S;
         }
     }
-    // Sort key: [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2], c = cell coordinate,
-    // s = which half of the cell (sub-cell bit).
-    __device__ __forceinline__ unsigned long long key_of(const uint32_t c[3], const uint32_t off[3]) const
+    // Sort key of a point (KeyT: uint32 when the key has at most 32 bits).
+    template <typename KeyT>
+    __device__ __forceinline__ KeyT key_of(const uint32_t c[3], const uint32_t off[3]) const
     {
-        unsigned long long k = 0;
-        uint32_t sub = 0;
+        KeyT k = 0;
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            k = (k << bits[p]) | sel3(c, perm[p]);
-            sub = (sub << 1) | (sel3(off, perm[p]) >= (uint32_t)h ? 1u : 0u);
-        }
-        return (k << 3) | sub;
+        for (int a = 0; a < 3; ++a)
+            k |= ((KeyT)c[a] << ksh[a]) | ((KeyT)(off[a] >= (uint32_t)h ? 1u : 0u) << kbit[a]);
+        return k;
     }
     // Sort payload of the packed layout: the original index in the low 32
     // bits and the point's offsets inside its cell (original axes x, y, z,
@@ -223,19 +220,12 @@ struct GridMap {
                ((unsigned long long)off[1] << 42) | ((unsigned long long)off[2] << 52);
     }
     // Inverse of key_of() + payload_of(): the quantised coordinates of a point.
-    __device__ __forceinline__ void unpack(unsigned long long key, unsigned long long v,
-                                           int32_t q[3]) const
+    template <typename KeyT>
+    __device__ __forceinline__ void unpack(KeyT key, unsigned long long v, int32_t q[3]) const
     {
-        unsigned long long ck = key >> 3;
-        uint32_t cp[3];
-#pragma unroll
-        for (int p = 2; p >= 0; --p) {
-            cp[p] = (uint32_t)(ck & ((1ull << bits[p]) - 1));
-            ck >>= bits[p];
-        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const uint32_t c = perm[0] == a ? cp[0] : (perm[1] == a ? cp[1] : cp[2]);
+            const uint32_t c = (uint32_t)((key >> ksh[a]) & (((KeyT)1 << kwid[a]) - 1));
             q[a] = lo[a] + (int32_t)(c * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
         }
     }

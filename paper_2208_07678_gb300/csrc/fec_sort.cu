@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
                 for (int a = 0; a < 3; ++a) quantize1(f[3 * r + a], q[a]);
                 uint32_t c[3], off[3];
                 gm.cell_of(q, c, off);
-                key[r] = (KeyT)gm.key_of(c, off);
+                key[r] = gm.key_of<KeyT>(c, off);
                 val[r] = (ValT)gm.payload_of(off, pos);
             }
         } else {
