@@ -418,10 +418,11 @@ def measure_serve(fec, duration=4.0, rate=400.0, pool=40, seed=5, slots_note="4 
                     lat.append(done_ns * 1e-9 - t0 - arrivals[j])
                 time.sleep(0.0005)
 
-        # warm every slot's workspace at once with the largest requests
+        # warm up as the plain path does (every pool request once), then the
+        # largest requests twice more, so that every slot has grown to them
         big = sorted(range(pool), key=lambda i: -reqs[i].n)[:4]
         warm = []
-        for i in big:
+        for i in list(range(pool)) + big + big:
             o = np.empty(reqs[i].n, np.int32)
             warm.append((ctx.submit(reqs[i].xyz, reqs[i].d, reqs[i].min_size, reqs[i].max_size, o), o))
         for t, _ in warm:

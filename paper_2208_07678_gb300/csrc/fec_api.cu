@@ -458,6 +458,20 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int6
 
 size_t ctx_budget(const fec_ctx *ctx) { return ctx->budget; }
 cudaStream_t ctx_stream(const fec_ctx *ctx) { return ctx->stream; }
+// Grows ctx's workspace to n points and a slab index of slab_cap entries
+// when that takes at most max_bytes (a serving slot grows once to the
+// largest request seen so far instead of again at every larger request).
+fec_status ctx_reserve(fec_ctx *ctx, size_t n, uint32_t slab_cap, size_t max_bytes)
+{
+    Workspace &ws = ctx->ws;
+    if (ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
+    Workspace probe;
+    probe.sms = ws.sms;
+    probe.list_scale = ws.list_scale;
+    const uint32_t sc = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
+    if (workspace_layout(probe, nullptr, n, sc) > max_bytes) return FEC_OK;
+    return ensure_workspace(ctx, n, slab_cap);
+}
 ServeEngine *ctx_serve(fec_ctx *ctx) { return ctx->serve; }
 
 }  // namespace fec

@@ -32,6 +32,7 @@
 namespace fec {
 
 cudaStream_t ctx_stream(const fec_ctx *ctx);  // fec_api.cu
+fec_status ctx_reserve(fec_ctx *ctx, size_t n, uint32_t slab_cap, size_t max_bytes);  // fec_api.cu
 
 namespace {
 
@@ -61,6 +62,8 @@ struct ServeEngine {
     int device = 0;
     size_t budget = 0;
     size_t in_flight = 0;
+    size_t hw_n = 0;         // largest request (points) and slab index seen so far
+    uint32_t hw_slab = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::mutex mu;
@@ -116,6 +119,17 @@ void ServeEngine::worker(int slot)
             if (!r) continue;
             in_flight += r->est;
         }
+        // grow this slot's workspace to the largest request seen so far (while
+        // that fits its share of the budget), so that slots do not each
+        // re-allocate as ever larger requests reach them
+        size_t hn = 0;
+        uint32_t hs = 0;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            hn = hw_n;
+            hs = hw_slab;
+        }
+        ctx_reserve(ctx, hn, hs, budget / kSlots);
         int32_t k = 0;
         const cudaStream_t st = ctx_stream(ctx);
         if (r->ready) cudaStreamWaitEvent(st, r->ready, 0);
@@ -233,6 +247,9 @@ fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, 
     {
         std::lock_guard<std::mutex> lk(e->mu);
         e->start();
+        if ((size_t)n > e->hw_n) e->hw_n = (size_t)n;
+        const uint32_t sc = make_params((uint32_t)n, d).slab_cap;
+        if (sc > e->hw_slab) e->hw_slab = sc;
         r->ticket = e->next_ticket++;
         e->all[r->ticket] = r;
         e->queue.push_back(r);
