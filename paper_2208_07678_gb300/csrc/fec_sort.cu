@@ -269,19 +269,22 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
 {
     const size_t smem = sizeof(SortSmem<KeyT, ValT>);
     static int per_sm = 0;  // resident blocks per SM (persistent grid)
+    constexpr bool kXyz = sizeof(ValT) == 8;  // keys from coordinates: packed payloads only
     if (!per_sm) {
         cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int a = 0, b = 0;
+        int a = 0, b = 1 << 30;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_onesweep<KeyT, ValT, false>,
                                                           kSortThreads, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep<KeyT, ValT, true>,
-                                                              kSortThreads, smem);
+        if constexpr (kXyz) {
+            const cudaError_t e2 = cudaFuncSetAttribute(
+                k_onesweep<KeyT, ValT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 != cudaSuccess) return e2;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_onesweep<KeyT, ValT, true>,
+                                                                  kSortThreads, smem);
+        }
         per_sm = (e != cudaSuccess || a < 1 || b < 1) ? 1 : (a < b ? a : b);
     }
     grid *= per_sm;
@@ -296,11 +299,16 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
     KeyT *kin = (KeyT *)ka_, *kout = (KeyT *)kb_;
     ValT *vin = (ValT *)va_, *vout = (ValT *)vb_;
     for (int p = 0; p < max_passes; ++p) {
-        if (p == 0 && src.xyz)
-            k_onesweep<KeyT, ValT, true><<<grid, kSortThreads, smem, st>>>(
-                ctl, nullptr, nullptr, kout, vout, tile_status, tstride, p, status, src.xyz,
-                src.plan, src.prm);
-        else
+        bool done = false;
+        if constexpr (kXyz) {
+            if (p == 0 && src.xyz) {
+                k_onesweep<KeyT, ValT, true><<<grid, kSortThreads, smem, st>>>(
+                    ctl, nullptr, nullptr, kout, vout, tile_status, tstride, p, status, src.xyz,
+                    src.plan, src.prm);
+                done = true;
+            }
+        }
+        if (!done)
             k_onesweep<KeyT, ValT, false><<<grid, kSortThreads, smem, st>>>(
                 ctl, kin, (p == 0 && identity_vals) ? nullptr : vin, kout, vout, tile_status,
                 tstride, p, status, nullptr, nullptr, src.prm);
