@@ -1,0 +1,113 @@
+"""Host-side logic of bench.py (no GPU): clock-sample summaries, the guard on
+committed DRAM-traffic figures, the algorithmic-byte table and the bounded
+oracle sample."""
+import importlib.util
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _sample_line(ts, sm, sm_max, power_cap="Not Active", hw="Not Active"):
+    stamp = time.strftime("%Y/%m/%d %H:%M:%S", time.localtime(ts)) + ".%03d" % int((ts % 1) * 1000)
+    return f"{stamp}, 0, {sm}, {sm_max}, 900.5, 0x0, {hw}, Not Active, Not Active, {power_cap}\n"
+
+
+def test_clock_summary_keeps_samples_inside_timed_windows(bench, tmp_path):
+    now = time.time()
+    p = tmp_path / "clocks.csv"
+    p.write_text(_sample_line(now - 10, 1200, 2070) +              # warm-up, outside
+                 _sample_line(now + 0.1, 2070, 2070) +
+                 _sample_line(now + 0.2, 2055, 2070, power_cap="Active") +
+                 _sample_line(now + 0.3, 2070, 2070) +
+                 _sample_line(now + 20, 900, 2070, hw="Active"))   # after, outside
+    cs = bench.ClockSampler(0)
+    cs.path = str(p)
+    cs.mark(now, now + 1.0)
+    s = cs.summary()
+    assert s["samples"] == 3 and s["window"] == "timed steps"
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]   # hw_slowdown was outside the window
+    assert not p.exists()                      # the temporary file is removed
+
+
+def test_clock_summary_without_samples_in_window_says_so(bench, tmp_path):
+    now = time.time()
+    p = tmp_path / "clocks.csv"
+    p.write_text(_sample_line(now - 5, 1800, 2070) + _sample_line(now - 4, 1900, 2070))
+    cs = bench.ClockSampler(0)
+    cs.path = str(p)
+    cs.mark(now, now + 1.0)
+    s = cs.summary()
+    assert s["samples"] == 2 and s["window"].startswith("whole measurement")
+    assert s["sm_mhz"] == 1850.0
+
+
+def test_clock_summary_unsampled(bench):
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["unsampled"]
+
+
+def test_traffic_is_dropped_once_the_kernel_source_changes(bench, monkeypatch):
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        j = json.load(f)
+    entry = j["map_27m"]["k_region"]
+    monkeypatch.setattr(bench, "source_hash", lambda fname: entry["source_sha"])
+    assert bench.ncu_traffic("k_region", "map_27m") == entry["bytes_per_launch"]
+    monkeypatch.setattr(bench, "source_hash", lambda fname: "0" * 16)
+    assert bench.ncu_traffic("k_region", "map_27m") is None
+    assert bench.ncu_traffic("k_region", "no_such_workload") is None
+
+
+def test_committed_traffic_is_consistent_with_the_algorithmic_bytes(bench):
+    """The full-map figure is the small capture scaled by the algorithmic
+    bytes; both sit a little above those bytes (no gross re-reads)."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        j = json.load(f)
+    # sizes of the two workloads (cells, sub-cells), as the bench reports them
+    small = bench.KERNEL_BYTES["k_region"](12_141_972, 2_373_102, 833_547)
+    full = bench.KERNEL_BYTES["k_region"](27_930_995, 5_459_358, 1_895_339)
+    ts, tf = j["map_frames:100"]["k_region"]["bytes_per_launch"], j["map_27m"]["k_region"]["bytes_per_launch"]
+    assert 1.0 <= ts / small <= 1.5
+    assert tf == pytest.approx(ts * full / small, rel=1e-6)
+
+
+def test_algorithmic_bytes_table(bench):
+    kb = bench.KERNEL_BYTES
+    n, Ms, Mc = 1000, 300, 100
+    assert kb["k_region"](n, Ms, Mc) == 88 * Mc + 52 * Ms
+    assert kb["onesweep_u32"](n, Ms, Mc) == 24 * n       # key 4 + payload 8, read and written
+    assert kb["k_keys"](n, Ms, Mc) == 12 * n             # coordinates read, histograms only
+    for name, f in kb.items():
+        assert f(2 * n, 2 * Ms, 2 * Mc) == 2 * f(n, Ms, Mc), name   # linear in the sizes
+        assert name in bench.KERNEL_SOURCE
+
+
+def test_oracle_sample_is_a_bounded_density_preserving_crop(bench):
+    from paper_2208_07678_gb300 import synth
+
+    cloud = synth.map_27m(n_frames=24)   # long enough for the density to be even along x
+    sample, desc = bench.oracle_sample(cloud, cloud.n // 4)
+    assert 0 < sample.n < cloud.n and "x-window crop" in desc
+    assert 0.5 * cloud.n / 4 < sample.n < 2.0 * cloud.n / 4
+    x = sample.xyz[:, 0]
+    assert np.all((x >= x.min()) & (x <= x.max()))
+    whole, desc2 = bench.oracle_sample(cloud, cloud.n + 1)
+    assert whole is cloud and desc2.startswith("whole cloud")
+
+
+def test_unknown_workload_is_refused(bench):
+    with pytest.raises(SystemExit):
+        bench.make_workload("no_such_workload")
