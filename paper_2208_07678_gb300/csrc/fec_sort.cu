@@ -1,16 +1,18 @@
-// fec_sort.cu -- LSD radix sort of (key, uint32 value) pairs, one kernel per
-// 8-bit digit ("onesweep": every tile ranks its keys stably in shared memory,
-// finds its global digit offsets by decoupled look-back over the preceding
-// tiles, and writes each digit run coalesced).  Replaces the kd-tree build of
-// Algorithm 1 (Section 2.2): sorting by grid-cell key groups every cell's
-// points contiguously.
+// fec_sort.cu -- LSD radix sort of (key, value) pairs (32- or 64-bit each),
+// one kernel per 8-bit digit ("onesweep": every tile ranks its keys stably in
+// shared memory, finds its global digit offsets by decoupled look-back over
+// the preceding tiles, and writes each digit run coalesced).  Replaces the
+// kd-tree build of Algorithm 1 (Section 2.2): sorting by grid-cell key groups
+// every cell's points contiguously.
 //
-// Digit histograms of all passes are computed up front (fused into the key
-// kernel for the main sort), so a pass reads each key and value once and
-// writes them once.  Look-back waits are bounded (kWaitCap); a timeout sets
-// ST_WAIT_TIMEOUT and the pass continues with a wrong prefix instead of
-// hanging.  Tile ids are taken from an atomic counter, so a tile only ever
-// waits on tiles already owned by running blocks.
+// Digit histograms of all passes are computed up front (by the key kernel
+// for the main sort), so a pass reads each key and value once and writes them
+// once; with packed payloads the main sort's first pass reads the point
+// coordinates instead and computes each key and payload itself.  Look-back
+// waits are bounded (kWaitCap); a timeout sets ST_WAIT_TIMEOUT and the pass
+// continues with a wrong prefix instead of hanging.  Tile ids are taken from
+// an atomic counter, so a tile only ever waits on tiles already owned by
+// running blocks.
 #include "fec_internal.cuh"
 
 namespace fec {
