@@ -258,19 +258,22 @@ def run_reference(args):
         return 0
     cloud = make_workload(args.workload)
     target = args.ref_points
-    vals = []
+    vals, secs = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
-        v, desc, _, _ = time_oracle(cloud, target)
+        v, desc, _, dt = time_oracle(cloud, target)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(dt)
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(secs),  # one step = the bounded sample
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "n": cloud.n, "d": cloud.d, "min_size": cloud.min_size,
-                   "max_size": cloud.max_size, "sample": desc},
+                   "max_size": cloud.max_size, "sample": desc, "parallelism": "1 host core"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
