@@ -557,6 +557,13 @@ def run_ours(args):
     step_total_ms = sum(t["total_ms"] for t in trace) / args.steps
     breakdown = {t["name"]: round(t["total_ms"] / args.steps, 4) for t in
                  sorted(trace, key=lambda t: -t["total_ms"])}
+    # the whole path against its compulsory traffic: 88 bytes per point and
+    # 16 per occupied cell, each array touched once
+    alg_path = 88 * n + 16 * Mc
+    whole = {"alg_bytes": alg_path, "achieved_gbs": alg_path / (ms_dev_max * 1e-3) / 1e9,
+             "peak_gbs": peak, "frac": alg_path / (ms_dev_max * 1e-3) / 1e9 / peak}
+    region = [t for t in trace if t["name"] == "k_region"]
+    region_s = region[0]["total_ms"] / region[0]["launches"] * 1e-3 if region else None
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -589,9 +596,13 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "whole_path": whole,
             "union_work": {k: stats[k] for k in ("pair_checks", "pair_box_joins", "pair_point_tests",
                                                  "pair_same_root", "point_evals",
                                                  "pairs_queued", "boundary_edges")},
+            # sub-cell pair decisions (box tests and joined-pair skips) per second of k_region
+            "pair_decisions_per_s": ((stats["pair_checks"] + stats["pair_same_root"]) / region_s
+                                     if region_s else None),
             **extra,
             "trace_ms_per_step": {"total": round(step_total_ms, 4), "traced_step_ms": ms_traced,
                                   "by_kernel": breakdown},
