@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.paper_fec import canonical, paper_fec_serial
+from oracle.paper_fec import canonical, compare_with_exact, paper_fec_serial, paper_fec_serial_kd
 from paper_2208_07678_gb300 import synth
 from tests._util import (INT64_MAX, boundary_pairs, check_labels_valid, fixtures, quantize_np,
                          random_cloud, scipy_labels, threshold_np)
@@ -217,3 +217,34 @@ def test_pairs_at_the_threshold(d):
     assert k == int(joined.sum()) + 2 * int((~joined).sum())
     np.testing.assert_array_equal(labels[:m] == labels[m:], joined)
 
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_serial_kd_loop_equals_plain_loop(seed):
+    """The kd-tree FindNeighbor gives the same Algorithm 1 labels as the
+    all-points scan."""
+    rng = np.random.default_rng([seed, 31])
+    n = int(rng.integers(1, 400))
+    q = rng.integers(-3000, 3000, size=(n, 3))
+    T2 = int(rng.integers(1, 400_000))
+    np.testing.assert_array_equal(canonical(paper_fec_serial(q, T2)),
+                                  canonical(paper_fec_serial_kd(q, T2)))
+
+
+def test_serial_segments_refine_exact_components():
+    """Algorithm 1 only merges along edges, so each of its segments lies in
+    one exact component; it may split a component, never join two."""
+    xyz = random_cloud(5, 3000, extent=10.0, clumps=12)
+    q, T2 = oracle.quantize(xyz), oracle.threshold(0.3)
+    comp = oracle.components(q, T2)
+    seg = paper_fec_serial_kd(q, T2)
+    for s in np.unique(seg):
+        assert np.unique(comp[seg == s]).size == 1
+    assert np.unique(seg).size >= np.unique(comp).size
+
+
+def test_serial_report_on_the_counterexample():
+    xyz = np.array([[0, 0, 0], [3, 0, 0], [1, 0, 0], [2, 0, 0]], dtype=np.float32)
+    r = compare_with_exact(xyz, 1.0)
+    assert (r["k_exact"], r["k_serial"], r["components_split"], r["points_in_split_components"]) == (1, 2, 1, 4)
+    assert r["points_kept_state_differs"] == 0
