@@ -55,8 +55,8 @@ KERNEL_BYTES = {
     "k_keys": lambda n, Ms, Mc: 12 * n,   # packed layout: histograms only, the sort's first pass makes the keys
     "onesweep_u32": lambda n, Ms, Mc: 24 * n,
     "k_cells": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
-    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 72 * Ms,
-    "k_region": lambda n, Ms, Mc: 88 * Mc + 52 * Ms,
+    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 60 * Ms,
+    "k_region": lambda n, Ms, Mc: 88 * Mc + 40 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
     "k_labels": lambda n, Ms, Mc: 16 * n + 4 * Ms,
 }

@@ -116,7 +116,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     const size_t lists = 2 * n * (size_t)(ws.list_scale ? ws.list_scale : 1);
     ws.pairq_cap = lists;
     ws.pairq = (uint2 *)take(sizeof(uint2) * lists);
-    ws.reps = (Rec *)take(sizeof(Rec) * n);
+    ws.reps = (uint32_t *)take(4 * n);
     // dense column index: 2^col_bits entries, about 4 per point (64 Ki..64 Mi)
     uint32_t cb = 16;
     while (cb < 26 && ((size_t)1 << cb) < 4 * n) ++cb;

@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(256)
                     const uint32_t *__restrict__ sc_start, SubBox *__restrict__ box,
                     uint32_t *__restrict__ sminidx, uint32_t *__restrict__ parent,
                     uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
-                    int32_t *__restrict__ crank, uint32_t *__restrict__ big, Rec *__restrict__ reps)
+                    int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps)
 {
     const uint32_t M = plan->M_s;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(256)
             atomicOr(&plan->status, ST_SIZE_OVERFLOW);
             box[a] = SubBox{0, 0, 0, 0, 0, 0, 0, 0};
             sminidx[a] = 0;
-            reps[a] = Rec{0, 0, 0, 0};
+            reps[a] = kNoRep;
             continue;
         }
         if (e - s > (uint32_t)kBigSubcell) {
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(256)
         b.count = e - s;
         box[a] = b;
         sminidx[a] = mi;
-        reps[a] = rp;
+        reps[a] = pack_rep(rp, b.lx, b.ly, b.lz);
     }
 }
 
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_subcell_big(Plan *plan, Params prm, const Rec *__restrict__ rec,
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps)
 {
     const uint32_t nb = plan->n_big;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(256)
             b.count = e - s;
             box[a] = b;
             sminidx[a] = mi;
-            reps[a] = rec[s + (uint32_t)bk];
+            reps[a] = pack_rep(rec[s + (uint32_t)bk], b.lx, b.ly, b.lz);
         }
     }
 }
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_subcell_huge(Plan *plan, Params prm, const Rec *__restrict__ rec,
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, Rec *__restrict__ reps)
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps)
 {
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(256)
             b.count = e - s;
             box[a] = b;
             sminidx[a] = m;
-            reps[a] = rec[s + (uint32_t)kk];
+            reps[a] = pack_rep(rec[s + (uint32_t)kk], b.lx, b.ly, b.lz);
         }
         __syncthreads();
     }

@@ -231,6 +231,17 @@ struct GridMap {
     }
 };
 
+// A sub-cell's representative point, stored as its offset from the low corner
+// of the sub-cell's box, 10 bits per axis (4 bytes instead of a 16-byte
+// record); kNoRep when an offset does not fit (boxes over 1,022 units wide,
+// possible only for d above 1 m), which leaves the pair to the point tests.
+constexpr uint32_t kNoRep = 0xffffffffu;
+__device__ __forceinline__ uint32_t pack_rep(const Rec &r, int32_t lx, int32_t ly, int32_t lz)
+{
+    const uint32_t ox = (uint32_t)(r.x - lx), oy = (uint32_t)(r.y - ly), oz = (uint32_t)(r.z - lz);
+    return (ox < 1023u && oy < 1023u && oz < 1023u) ? (ox | (oy << 10) | (oz << 20)) : kNoRep;
+}
+
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
     uint32_t v;
@@ -349,7 +360,7 @@ struct Workspace {
     uint32_t *slab_lo = nullptr;   // slab_cap
     uint32_t *slab_hi = nullptr;
     uint2 *pairq = nullptr;        // sub-cell pairs queued for point tests
-    Rec *reps = nullptr;           // per sub-cell: its point nearest the box centre
+    uint32_t *reps = nullptr;      // per sub-cell: its point nearest the box centre (pack_rep)
     uint32_t *col_lo = nullptr;    // dense column index: cells of column (c0, c1) are
     uint32_t *col_hi = nullptr;    //   [col_lo, col_hi) of the sorted cell array
     uint32_t col_bits = 0;         // log2 of its capacity

@@ -179,11 +179,16 @@ __device__ __noinline__ bool thread_pair_test(uint32_t a, uint32_t b, const SubB
 // d), 1 = edge (box diameter within d, or the two representatives within
 // d), 2 = undecided (needs point tests).
 template <bool WIDE>
-__device__ __forceinline__ int box_decide(const SubBox &A, const SubBox &B, const Rec &ra,
-                                          const Rec &rb, const Metric<WIDE> &m)
+__device__ __forceinline__ int box_decide(const SubBox &A, const SubBox &B, uint32_t ra,
+                                          uint32_t rb, const Metric<WIDE> &m)
 {
     if (!m.box_gap(A, B)) return 0;
-    if (m.box_diam(A, B) || m.within(ra.x - rb.x, ra.y - rb.y, ra.z - rb.z)) return 1;
+    if (m.box_diam(A, B)) return 1;
+    if (ra != kNoRep && rb != kNoRep &&  // the two representatives (packed, see pack_rep)
+        m.within((A.lx + (int)(ra & 1023u)) - (B.lx + (int)(rb & 1023u)),
+                 (A.ly + (int)((ra >> 10) & 1023u)) - (B.ly + (int)((rb >> 10) & 1023u)),
+                 (A.lz + (int)(ra >> 20)) - (B.lz + (int)(rb >> 20))))
+        return 1;
     return 2;
 }
 
@@ -447,7 +452,7 @@ template <bool WIDE>
 __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     k_region(Plan *plan, Params prm, const unsigned long long *__restrict__ cell_key,
              const uint32_t *__restrict__ cell_sc, const SubBox *__restrict__ box,
-             const Rec *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
+             const uint32_t *__restrict__ reps, const Rec *__restrict__ rec, uint32_t *parent,
              const uint32_t *__restrict__ nb_first, const uint8_t *__restrict__ nb_cnt,
              uint2 *__restrict__ pairq, uint32_t qcap, uint2 *__restrict__ edges, uint32_t ecap,
              uint32_t *__restrict__ scratch, uint32_t scap)
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 b = S.qb[w][lane];
                 local = b - s0 < ns;
                 const SubBox BA = box[a], BB = box[b];
-                const Rec RA = reps[a], RB = reps[b];
+                const uint32_t RA = reps[a], RB = reps[b];
                 if (local && s_find(vpar, a - s0) == s_find(vpar, b - s0)) {
                     ++n_same;
                 } else {
