@@ -74,3 +74,12 @@ def test_multiply_shift_division_is_exact(S):
     rel = np.arange(1 << 24, dtype=np.uint64)
     got = (rel * np.uint64(m)) >> np.uint64(s)
     np.testing.assert_array_equal(got, rel // np.uint64(S))
+
+
+def test_cell_keys_fit_for_one_centimetre_over_eight_kilometres():
+    """The documented limit: for d >= 1 cm over an 8 km cube the cell key needs
+    at most 61 bits (3 axes of bitlen(extent / S)), plus the 3-bit sub-cell code."""
+    ext = 8000 * 1024
+    for d in [0.01, 0.0101, 0.015, 0.02, 0.1, 1.0, 10.0]:
+        _, _, _, S = grid_of(d)
+        assert 3 * (ext // S).bit_length() <= 61, d
