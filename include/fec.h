@@ -168,6 +168,24 @@ fec_status fec_trace_enable(fec_ctx *ctx, int enable);
  * returns the number of distinct names, or -1 on a bad argument. */
 int fec_trace_read(const fec_ctx *ctx, fec_trace_entry *out, int cap);
 
+/* Failure-path control.  Every loop on the device that waits on other
+ * blocks (the decoupled look-back of the radix sort and of the cell-table
+ * scan) or walks the global union-find (finds, unions and the flatten) is
+ * bounded: after wait_cap spin iterations, or union_cap steps, it gives up,
+ * the call's remaining kernels return at once, and the call returns
+ * FEC_ERR_NOT_CONVERGED with its labels unspecified (never FEC_OK with wrong
+ * labels).  The caps of the Section 2.2 pipeline are FEC_DEFAULT_WAIT_CAP
+ * and FEC_DEFAULT_UNION_CAP, far above what any correct run needs; this call
+ * sets them for later fec_cluster calls on ctx (not the batch or serving
+ * paths), so that tests can make a wait or a union run out on purpose
+ * (wait_cap 0: any wait gives up at once; union_cap 0: any find that has to
+ * walk, or any union, gives up).  The device and the context stay usable:
+ * set the defaults back and the next call is exact again.  Thread-compatible
+ * like fec_cluster. */
+#define FEC_DEFAULT_WAIT_CAP ((uint32_t)1 << 22)
+#define FEC_DEFAULT_UNION_CAP ((uint32_t)1 << 20)
+fec_status fec_set_iteration_caps(fec_ctx *ctx, uint32_t wait_cap, uint32_t union_cap);
+
 /* Device workspace bytes fec_cluster needs for n points at radius d. */
 int64_t fec_workspace_bytes(int64_t n, float d);
 
@@ -191,12 +209,17 @@ int64_t fec_workspace_bytes(int64_t n, float d);
  *                FEC_ERR_OUT_OF_RANGE, and one that needs more boundary
  *                lists than the array holds gives FEC_ERR_OOM.
  *   cuda_stream  cudaStream_t to run on (NULL = the default stream).
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's contents: each call clears what must start at zero, and calls
- * are serialised inside the library and return only when their GPU work is
- * done, because calls whose GPU work overlapped would race on the array. */
+ * The first call on each device does a set-up step: it looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current), which is
+ * then reused; make that first call before any stream capture begins.  The
+ * address belongs to the CUDA context it was taken in, so the set-up is
+ * repeated when a later call finds a different context current on the device
+ * (the caller's own context, or a new one after cudaDeviceReset).  All calls
+ * share the one array, which keeps the last call's contents: each call clears
+ * what must start at zero, and calls are serialised inside the library and
+ * return only when their GPU work is done (the call synchronises
+ * cuda_stream), because calls whose GPU work overlapped would race on the
+ * array. */
 fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, int64_t min_size,
                                int64_t max_size, int32_t *labels, int32_t *num_clusters,
                                void *cuda_stream);

@@ -103,6 +103,36 @@ def cluster(xyz, d: float, min_size: int = 1, max_size: int = INT64_MAX):
     return _cluster("fec_oracle_cluster", xyz, d, min_size, max_size)
 
 
+def _cluster_job(job):
+    xyz, d, min_size, max_size = job
+    return cluster(xyz, d, min_size, max_size)
+
+
+def cluster_many(jobs, processes=None):
+    """cluster() over independent clouds [(xyz, d, min_size, max_size), ...]
+    in a pool of worker processes (one per host core by default), in order.
+    The pool is started with ``spawn``, so it is safe in a process that
+    already uses the GPU.  Returns [(labels, k), ...]."""
+    import multiprocessing as mp
+
+    jobs = list(jobs)
+    if not jobs:
+        return []
+    procs = processes or os.cpu_count() or 1
+    procs = max(1, min(procs, len(jobs)))
+    if procs == 1:
+        return [_cluster_job(j) for j in jobs]
+    build()  # compile once here, not in every worker
+    # largest clouds first, so that no worker is left with a big one at the end
+    order = sorted(range(len(jobs)), key=lambda i: -np.asarray(jobs[i][0]).size)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_cluster_job, [jobs[i] for i in order], chunksize=1)
+    out = [None] * len(jobs)
+    for i, r in zip(order, res):
+        out[i] = r
+    return out
+
+
 def bruteforce(xyz, d: float, min_size: int = 1, max_size: int = INT64_MAX):
     """O(n^2) all-pairs union-find oracle (tiny inputs only)."""
     return _cluster("fec_oracle_bruteforce", xyz, d, min_size, max_size)

@@ -1,25 +1,28 @@
-"""Algorithm 1 (FEC's serial point-wise loop) as printed, for comparison only.
+"""FEC's serial point-wise scheme, for comparison with the exact components.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Algorithm 1 visits the points in index order.  A still-unlabelled point p_i
-queries its neighbours within d, takes the smallest non-zero neighbour label
-(or a fresh segment label), and rewrites every larger neighbour label across
-the whole cloud (the segment-merge loop).  As printed, the loop never writes
-the chosen label into p_i or into unlabelled neighbours; this restatement
-reads it as doing so (otherwise no point is ever labelled).
+Section 2 describes FEC as a point-wise scheme: points are visited in their
+input order, and only a point that no earlier visit has put into a segment
+looks for its neighbours within d (FindNeighbor, Algorithm 1).  The segments
+already present around it are merged into the one with the smallest segment
+number (a fresh number when there is none), and the neighbours that had no
+segment join it.  The printed listing leaves the chosen number unwritten for
+the visiting point and its unlabelled neighbours; this module reads it as
+writing it (otherwise no point would ever be labelled).
 
-Because only still-unlabelled points issue queries, an edge between two points
-that were both labelled by earlier queries is never examined.  The result can
-therefore split a connected component, which is why the library computes exact
-connected components instead (the oracle in ``fec_oracle.c``).  The tests use
-this routine to demonstrate that difference on a four-point example.
+Here the scheme is kept as a partition of segment numbers (a small
+union-find whose root is the smallest number of each merged group) instead of
+relabelling the whole cloud at every merge; the partition it yields is the
+same.  Because only points without a segment issue queries, an edge between
+two points that earlier visits both put into segments is never examined: the
+result can split a connected component of the distance graph, which is why
+the library computes exact components (the oracle in ``fec_oracle.c``).
 
-``paper_fec_serial`` is pure Python, O(n) per query: tiny inputs only.
-``paper_fec_serial_kd`` runs the same loop with FindNeighbor answered by a
-kd-tree (scipy), for clouds of tens of thousands of points, and
-``compare_with_exact`` reports how its size-filtered segments differ from the
-exact components.
+``paper_fec_serial`` answers each neighbour query by brute force (tiny
+inputs only); ``paper_fec_serial_kd`` by a kd-tree (scipy), for clouds of
+tens of thousands of points; ``compare_with_exact`` reports how the
+size-filtered segments differ from the exact components.
 """
 from __future__ import annotations
 
@@ -28,27 +31,55 @@ import math
 import numpy as np
 
 
-def paper_fec_serial(q: np.ndarray, T2: int) -> np.ndarray:
-    """Labels (1-based segment labels, Algorithm 1) from int coordinates q[n,3]."""
-    q = np.asarray(q, dtype=np.int64).reshape(-1, 3)
-    n = q.shape[0]
-    lab = np.zeros(n, dtype=np.int64)
-    seg = 1
+class _Segments:
+    """Segment numbers 1, 2, ... under merging; the representative of a
+    merged group is its smallest number."""
+
+    def __init__(self):
+        self.up = [0]  # up[s] == s for a representative; slot 0 is unused
+
+    def new(self) -> int:
+        self.up.append(len(self.up))
+        return len(self.up) - 1
+
+    def rep(self, s: int) -> int:
+        while self.up[s] != s:
+            self.up[s] = self.up[self.up[s]]
+            s = self.up[s]
+        return s
+
+    def merge_into(self, keep: int, others) -> None:
+        for o in others:
+            self.up[self.rep(o)] = keep
+
+
+def _pointwise(n: int, neighbours) -> np.ndarray:
+    """The point-wise scheme over points 0..n-1; neighbours(i) returns the
+    indices within d of point i (i included).  Returns 1-based labels."""
+    seg = np.zeros(n, dtype=np.int64)  # 0: no segment yet
+    segs = _Segments()
     for i in range(n):
-        if lab[i] != 0:
+        if seg[i]:
             continue
-        d2 = ((q - q[i]) ** 2).sum(axis=1)
-        nn = np.nonzero(d2 <= T2)[0]  # FindNeighbor(p_i, d), p_i included
-        nonzero = [lab[j] for j in nn if lab[j] != 0]
-        m = min(nonzero + [seg]) if nonzero else seg
-        for j in nn:
-            old = lab[j]
-            if old > m:  # segment merge: rewrite that label everywhere
-                lab[lab == old] = m
-            elif old == 0:
-                lab[j] = m
-        seg += 1
-    return lab
+        near = neighbours(i)
+        fresh = segs.new()
+        present = {segs.rep(int(s)) for s in seg[near] if s}
+        keep = min(present | {fresh})
+        segs.merge_into(keep, present | {fresh})
+        free = near[seg[near] == 0]
+        seg[free] = keep
+    return np.array([segs.rep(int(s)) for s in seg], dtype=np.int64)
+
+
+def paper_fec_serial(q: np.ndarray, T2: int) -> np.ndarray:
+    """Segment labels of the point-wise scheme from int coordinates q[n,3],
+    neighbours by brute force (join iff squared distance <= T2)."""
+    q = np.asarray(q, dtype=np.int64).reshape(-1, 3)
+
+    def neighbours(i):
+        return np.nonzero(((q - q[i]) ** 2).sum(axis=1) <= T2)[0]
+
+    return _pointwise(q.shape[0], neighbours)
 
 
 def canonical(labels: np.ndarray) -> np.ndarray:
@@ -71,30 +102,20 @@ def paper_fec_serial_kd(q: np.ndarray, T2: int) -> np.ndarray:
 
     q = np.asarray(q, dtype=np.int64).reshape(-1, 3)
     n = q.shape[0]
-    lab = np.zeros(n, dtype=np.int64)
     if n == 0:
-        return lab
+        return np.zeros(0, dtype=np.int64)
     tree = cKDTree(q.astype(np.float64))
     r = math.sqrt(float(T2)) + 1.0
-    seg = 1
-    for i in range(n):
-        if lab[i] != 0:
-            continue
-        cand = np.sort(np.asarray(tree.query_ball_point(q[i].astype(np.float64), r), dtype=np.int64))
-        d2 = ((q[cand] - q[i]) ** 2).sum(axis=1)
-        nn = cand[d2 <= T2]
-        old = np.unique(lab[nn])
-        old = old[old != 0]
-        m = int(min(old.min(), seg)) if old.size else seg
-        for o in old[old > m]:  # segment merge: rewrite that label everywhere
-            lab[lab == o] = m
-        lab[nn[lab[nn] == 0]] = m
-        seg += 1
-    return lab
+
+    def neighbours(i):
+        cand = np.asarray(tree.query_ball_point(q[i].astype(np.float64), r), dtype=np.int64)
+        return cand[((q[cand] - q[i]) ** 2).sum(axis=1) <= T2]
+
+    return _pointwise(n, neighbours)
 
 
 def compare_with_exact(xyz, d: float, min_size: int = 1, max_size: int = (1 << 63) - 1) -> dict:
-    """Algorithm 1 as printed (serial, index order) against the exact
+    """The point-wise scheme (serial, index order) against the exact
     components on one cloud, both with the size bounds applied: cluster
     counts, exact components that the serial loop splits, and the points
     whose kept/dropped state or partner set differs."""

@@ -1,4 +1,4 @@
-"""Algorithm 1 as printed against the exact components, on seeded workloads.
+"""FEC's serial point-wise scheme against the exact components, on seeded workloads.
 
 TEST INFRASTRUCTURE ONLY (it runs the oracle).  Prints one Markdown table row
 per workload: cluster counts of the serial loop and of the exact components

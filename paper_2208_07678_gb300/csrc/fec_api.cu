@@ -1,5 +1,6 @@
 // fec_api.cu -- contexts, workspace, the one-cloud pipeline on a stream, and
 // the C ABI declared in include/fec.h.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -7,6 +8,8 @@
 #include <mutex>
 #include <new>
 #include <vector>
+
+#include <cuda.h>
 
 #include "fec.h"
 #include "fec_batch.h"
@@ -147,12 +150,13 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
 // Pipeline
 // ---------------------------------------------------------------------------
 
-cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
+cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm_in,
                             long long min_size, long long max_size, int32_t *labels,
                             cudaStream_t st)
 {
-    Params prm = make_params(n, d);
+    Params prm = prm_in;
     prm.col_bits = ws.col_bits;
+    const uint32_t n = prm.n;
     const int sort_grid = ws.sms;  // per SM; the sort multiplies by its occupancy
     cudaError_t e = enqueue_front(ws, xyz, prm, st);
     if (e != cudaSuccess) return e;
@@ -175,7 +179,7 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d
     if (e != cudaSuccess) return e;
     const int kp = kept_sort_passes(n);
     if (kp > 0) {
-        e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), ws.sms * 4, st);
+        e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), &ws.plan->status, ws.sms * 4, st);
         if (e != cudaSuccess) return e;
         FEC_MARK(ws, "hist_kept", st);
         e = launch_sort(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
@@ -284,6 +288,54 @@ void trace_mark(const Workspace &ws, const char *name, cudaStream_t st)
     ++t->used;
 }
 
+namespace {
+
+// Driver entry points for the current context's ID, taken through the
+// runtime once (no link against the driver library is needed).
+using PfnCtxGetCurrent = CUresult (*)(CUcontext *);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+std::once_flag g_pfn_once;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+}  // namespace
+
+unsigned long long current_ctx_id()
+{
+    std::call_once(g_pfn_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = (PfnCtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = (PfnCtxGetId)f;
+        cudaGetLastError();
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (g_ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+bool ctx_setup_needed(std::atomic<unsigned long long> &done_in)
+{
+    const unsigned long long id = current_ctx_id();
+    if (id != 0 && done_in.load(std::memory_order_acquire) == id) return false;
+    return true;
+}
+
+void ctx_setup_done(std::atomic<unsigned long long> &done_in)
+{
+    done_in.store(current_ctx_id(), std::memory_order_release);
+}
+
 int sm_count()
 {
     int dev = 0, v = 0;
@@ -310,6 +362,8 @@ struct fec_ctx {
     BatchEngine *batch = nullptr;
     Trace trace;
     bool tracing = false;
+    uint32_t wait_cap = kWaitCap;    // iteration caps of the device loops (fec_set_iteration_caps)
+    uint32_t union_cap = kUnionCap;
 };
 
 namespace {
@@ -397,7 +451,7 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
 
 namespace fec {
 
-fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_size,
                         int64_t max_size, int32_t *labels, int32_t *num_clusters,
                         const Params &prm);
 
@@ -405,13 +459,15 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int6
 fec_status cluster_locked(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
                           int64_t max_size, int32_t *labels, int32_t *num_clusters)
 {
-    const Params prm = make_params((uint32_t)n, d);
+    Params prm = make_params((uint32_t)n, d);
+    prm.wait_cap = ctx->wait_cap;
+    prm.union_cap = ctx->union_cap;
     fec_status s = ensure_workspace(ctx, (size_t)n, prm.slab_cap);
     if (s != FEC_OK) return s;
     // The boundary-edge and pair lists hold 2 entries per point; a cloud that
     // needs more (it is reported by the device) is re-run with larger lists.
     for (int attempt = 0;; ++attempt) {
-        s = cluster_once(ctx, xyz, n, d, min_size, max_size, labels, num_clusters, prm);
+        s = cluster_once(ctx, xyz, n, min_size, max_size, labels, num_clusters, prm);
         if (!(ctx->summary_host->status & ST_QUEUE_OVERFLOW) || attempt == 3) return s;
         ctx->ws.list_scale *= 4;
         s = ensure_workspace(ctx, (size_t)n, prm.slab_cap, true);
@@ -419,7 +475,7 @@ fec_status cluster_locked(fec_ctx *ctx, const float *xyz, int64_t n, float d, in
     }
 }
 
-fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
+fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_size,
                         int64_t max_size, int32_t *labels, int32_t *num_clusters,
                         const Params &prm)
 {
@@ -436,8 +492,7 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, float d, int6
     }
     const bool dev_out = is_device_ptr(labels);
     int32_t *lout = dev_out ? labels : ws.labels;
-    if (enqueue_cluster(ws, xin, (uint32_t)n, d, min_size, max_size, lout, ctx->stream) !=
-        cudaSuccess)
+    if (enqueue_cluster(ws, xin, prm, min_size, max_size, lout, ctx->stream) != cudaSuccess)
         return FEC_ERR_CUDA;
     if (!dev_out) {
         if (cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost,
@@ -607,6 +662,15 @@ fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offs
     ctx->last.n = offsets[nb];
     ctx->last.workspace_bytes = (int64_t)(ctx->ws.bytes + batch_bytes(ctx->batch));
     return s;
+}
+
+fec_status fec_set_iteration_caps(fec_ctx *ctx, uint32_t wait_cap, uint32_t union_cap)
+{
+    if (!ctx) return FEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->wait_cap = wait_cap;
+    ctx->union_cap = union_cap;
+    return FEC_OK;
 }
 
 fec_status fec_trace_enable(fec_ctx *ctx, int enable)

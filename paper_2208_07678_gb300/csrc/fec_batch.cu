@@ -291,8 +291,8 @@ fec_status capture(BatchEngine &e, int lanes, const float *xyz,
                 err = cudaMemsetAsync(e.res_dev + f, 0, sizeof(FrameResult), ln.st);
                 continue;
             }
-            err = enqueue_cluster(ln.ws, xyz + 3 * offsets[f], (uint32_t)n, d[f], mn[f], mx[f],
-                                  labels + offsets[f], ln.st);
+            err = enqueue_cluster(ln.ws, xyz + 3 * offsets[f], make_params((uint32_t)n, d[f]),
+                                  mn[f], mx[f], labels + offsets[f], ln.st);
             if (err == cudaSuccess) {
                 k_frame_result<<<1, 32, 0, ln.st>>>(ln.ws.plan, e.res_dev + f);
                 err = cudaGetLastError();

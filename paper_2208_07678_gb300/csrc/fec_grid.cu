@@ -34,7 +34,7 @@ __device__ __forceinline__ T warp_max(T v)
 }  // namespace
 
 // Reset the plan for a call of n points.
-__global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
+__global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes, uint32_t wait_cap)
 {
     const int t = threadIdx.x;
     if (t < 3) {
@@ -59,6 +59,8 @@ __global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes)
         plan->sort.npasses = 0;
         plan->sort.key64 = 0;
         plan->sort.parity = 0;
+        plan->sort.wait_cap = wait_cap;
+        plan->kept.wait_cap = wait_cap;
         plan->kept.n = 0;
         plan->kept.npasses = kept_passes;
         plan->kept.key64 = 0;
@@ -345,7 +347,8 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
 {
     const SortCtl *ctl = &plan->sort;
     const uint32_t n = ctl->n;
-    if (n == 0) return;
+    if (n == 0 || block_aborted(&plan->status)) return;
+    const uint32_t wait_cap = prm.wait_cap;
     const bool in_b = (ctl->npasses & 1u) != 0;
     const KeyT *__restrict__ keys = in_b ? keys_b : keys_a;
     const ValT *__restrict__ vals = in_b ? vals_b : vals_a;
@@ -451,7 +454,7 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
                     const int stop = incl_m ? __ffs(incl_m) - 1 : 31;
                     bool ready = (sv & ~kMask) != 0 || lane > stop;
                     while (!__all_sync(0xffffffffu, ready)) {
-                        if (++it > kWaitCap) {
+                        if (++it > wait_cap) {
                             if (lane == 0) atomicOr(&plan->status, ST_WAIT_TIMEOUT);
                             break;
                         }
@@ -467,7 +470,7 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
                     prefix += part;
-                    if (incl_m || it > kWaitCap) break;
+                    if (incl_m || it > wait_cap) break;
                     p -= 32;
                 }
                 if (lane == 0) st_relaxed64(tstat + tile, kIncl | ((prefix + tot) & kMask));
@@ -595,6 +598,7 @@ __global__ void __launch_bounds__(256)
                     uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
                     int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
@@ -654,6 +658,7 @@ __global__ void __launch_bounds__(256)
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
                   SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t nb = plan->n_big;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     const int l = threadIdx.x & 31;
@@ -711,6 +716,7 @@ __global__ void __launch_bounds__(256)
 {
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
+    if (block_aborted(&plan->status)) return;
     const uint32_t nb = plan->n_huge;
     big += plan->sort.n / 2;
     const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
@@ -786,7 +792,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_clear_cols(Plan *plan, uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi)
 {
-    if (!plan->use_cols) return;
+    if (!plan->use_cols || call_aborted(&plan->status)) return;
     const size_t ncol = (size_t)1 << (plan->bits[0] + plan->bits[1]);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ncol;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -802,6 +808,7 @@ __global__ void __launch_bounds__(256)
             uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
             uint8_t *__restrict__ cocc)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
     const uint32_t b2 = plan->bits[2];
     const uint32_t sh = plan->bits[1] + b2;
@@ -829,7 +836,7 @@ __global__ void __launch_bounds__(256)
 cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
 {
     const int grid = grid_for(ws, prm.n, 1024, 8);  // four points per thread
-    k_init<<<1, 256, 0, st>>>(ws.plan, prm.n, (uint32_t)kept_sort_passes(prm.n));
+    k_init<<<1, 256, 0, st>>>(ws.plan, prm.n, (uint32_t)kept_sort_passes(prm.n), prm.wait_cap);
     FEC_MARK(ws, "k_init", st);
     k_bbox<<<grid, 256, 0, st>>>(xyz, prm.n, ws.plan);
     FEC_MARK(ws, "k_bbox", st);

@@ -17,11 +17,14 @@
 // live in Plan / SortCtl in device memory; kernels read them and grid-stride.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <type_traits>
 
 #include <cuda_runtime.h>
+
+#include "fec.h"
 
 namespace fec {
 
@@ -35,6 +38,10 @@ enum : uint32_t {
     ST_SIZE_OVERFLOW = 1u << 5,    // a device count exceeded its buffer
     ST_QUEUE_OVERFLOW = 1u << 6,   // more boundary edges / pairs than the lists hold
 };
+// Status bits after which a call's remaining kernels return at once: a wait
+// or union loop gave up, or a device count went out of range, so later
+// stages would index through wrong offsets.
+constexpr uint32_t kAbortBits = ST_WAIT_TIMEOUT | ST_UNION_CAP | ST_SIZE_OVERFLOW;
 
 // Work counters of the union step (Plan::ctr).
 enum {
@@ -81,8 +88,10 @@ constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept pe
 constexpr uint32_t kRegionCellsPerBlock = FEC_REGION_CELLS;
 constexpr int kRegionThreads = FEC_REGION_THREADS;
 constexpr int kRegionBlocksPerSM = FEC_REGION_BLOCKS;
-constexpr uint32_t kWaitCap = 1u << 22;  // spin iterations before a wait gives up
-constexpr uint32_t kUnionCap = 1u << 20; // retries of one union before it gives up
+constexpr uint32_t kWaitCap = 1u << 22;  // default: spin iterations before a wait gives up
+constexpr uint32_t kUnionCap = 1u << 20; // default: steps of one union or find before it gives up
+static_assert(kWaitCap == FEC_DEFAULT_WAIT_CAP && kUnionCap == FEC_DEFAULT_UNION_CAP,
+              "the header's default caps");
 
 // Control block of one radix sort (device memory).
 struct SortCtl {
@@ -90,6 +99,7 @@ struct SortCtl {
     uint32_t npasses;   // 8-bit digit passes to run
     uint32_t key64;     // 1: 64-bit keys, 0: 32-bit keys
     uint32_t parity;    // pass p uses look-back array (p + parity) & 1, which starts clear
+    uint32_t wait_cap;  // spin iterations of a look-back wait before it gives up
     uint32_t hist[kMaxPasses][kRadixBins];   // digit counts of every pass
     uint32_t tile_counter[kMaxPasses];       // dynamic tile ids of every pass
 };
@@ -126,6 +136,8 @@ struct Params {
     uint32_t packed;     // 1: sort values carry the in-cell offsets (S <= 1024)
     // floor(rel / S) == (rel * div_m) >> div_s for every rel < 2^24
     uint32_t div_m, div_s;
+    uint32_t wait_cap = kWaitCap;    // iterations of a look-back wait before it gives up
+    uint32_t union_cap = kUnionCap;  // steps of a union or find before it gives up
 };
 
 // Quantised point record in cell order: coordinates and the original index.
@@ -279,13 +291,15 @@ __device__ __forceinline__ void spin_pause(uint32_t it)
 }
 
 // Union-find over sub-cells.  Invariant: parent[x] <= x, roots satisfy
-// parent[r] == r, so the root of a set is its smallest member.
-__device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x)
+// parent[r] == r, so the root of a set is its smallest member.  Every loop
+// takes at most `cap` steps; a walk cut short sets ok = false (the caller
+// flags ST_UNION_CAP, which stops the rest of the call).
+__device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x, uint32_t cap, bool &ok)
 {
     uint32_t cur = ld_relaxed(parent + x);
     if (cur == x) return x;
     uint32_t prev = x;
-    for (uint32_t it = 0; it < kUnionCap; ++it) {
+    for (uint32_t it = 0; it < cap; ++it) {
         uint32_t next = ld_relaxed(parent + cur);
         if (next == cur) return cur;
         // path halving: prev skips to cur's parent (still an ancestor)
@@ -293,16 +307,19 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x)
         prev = cur;
         cur = next;
     }
+    ok = false;
     return cur;
 }
 
 // Join the sets of a and b: hook the larger root under the smaller.
-// Returns false if the retry cap was hit (the caller flags ST_UNION_CAP).
-__device__ __forceinline__ bool uf_unite(uint32_t *parent, uint32_t a, uint32_t b)
+// Returns false if a loop hit its cap (the caller flags ST_UNION_CAP).
+__device__ __forceinline__ bool uf_unite(uint32_t *parent, uint32_t a, uint32_t b, uint32_t cap)
 {
-    for (uint32_t it = 0; it < kUnionCap; ++it) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
+    bool ok = true;
+    for (uint32_t it = 0; it < cap; ++it) {
+        a = uf_find(parent, a, cap, ok);
+        b = uf_find(parent, b, cap, ok);
+        if (!ok) return false;
         if (a == b) return true;
         if (a < b) {
             uint32_t t = a;
@@ -315,6 +332,23 @@ __device__ __forceinline__ bool uf_unite(uint32_t *parent, uint32_t a, uint32_t 
         a = old;
     }
     return false;
+}
+
+// True when an earlier stage of this call gave up (kAbortBits): the kernel
+// must return at once.  Read once at entry, so every block of a kernel that
+// waits on its peers decides the same way (blocks that start late and see
+// the bit take no tile, so no tile is left unpublished).
+__device__ __forceinline__ bool call_aborted(const uint32_t *status)
+{
+    return (*(volatile const uint32_t *)status & kAbortBits) != 0;
+}
+// The same decision taken once per block (thread 0 reads, every thread gets
+// its answer), for kernels with block barriers: a bit set by another block
+// between two threads' reads cannot split the block.  Every thread of the
+// block must call it.
+__device__ __forceinline__ bool block_aborted(const uint32_t *status)
+{
+    return __syncthreads_or(threadIdx.x == 0 && call_aborted(status)) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -441,8 +475,10 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
 // a6 rank + labels (labels: device pointer, n entries).
 cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool packed,
                            cudaStream_t st);
-// The whole pipeline for one cloud (device pointers), no host synchronisation.
-cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, uint32_t n, float d,
+// The whole pipeline for one cloud of prm.n points (device pointers), no host
+// synchronisation.  prm comes from make_params(n, d); callers may lower its
+// slab capacity or iteration caps.
+cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm,
                             long long min_size, long long max_size, int32_t *labels,
                             cudaStream_t st);
 
@@ -483,8 +519,19 @@ inline size_t sort_status_words(uint32_t max_n)
     return 2 * (((size_t)max_n + kSortTile - 1) / kSortTile + 1) * kRadixBins;
 }
 // Digit histograms of all passes for 32-bit keys already in memory.
-cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st);
+cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, const uint32_t *status, int grid,
+                            cudaStream_t st);
 
 int sm_count();
+
+// ID of the CUDA context current on this thread (unique within the process,
+// never reused), or 0 when it cannot be told.  Per-context set-up (function
+// attributes, symbol addresses) is keyed on it: a device reset or a second
+// device gives a new context, whose set-up must be done again.
+unsigned long long current_ctx_id();
+// True when the set-up recorded in done_in was not made in the current
+// context (or the context cannot be told); ctx_setup_done records it.
+bool ctx_setup_needed(std::atomic<unsigned long long> &done_in);
+void ctx_setup_done(std::atomic<unsigned long long> &done_in);
 
 }  // namespace fec

@@ -4,13 +4,18 @@
 //
 // The array below is part of the library's device image: every GPU that loads
 // the library holds it until the process exits.  Host code cannot use the
-// symbol as a device address, so the address is looked up once per device
-// with cudaGetSymbolAddress (with that device current) and passed to the
-// kernels.  Every call shares the array and leaves the last call's contents
-// in it; the pipeline clears what must start at zero at the start of each
-// call.  Calls are serialised by a host mutex and each returns only after
-// its GPU work has finished, because two calls whose work overlapped on the
-// GPU would race on the shared array.
+// symbol as a device address, so the address is looked up with
+// cudaGetSymbolAddress (with the device current) and passed to the kernels.
+// The lookup is a set-up step done on the first call on each device, and
+// again whenever the CUDA context current on that device is not the one the
+// cached address was taken in (a caller's own context, or a new primary
+// context after cudaDeviceReset): an address is valid only in the context
+// whose module it came from.  Contexts are told apart by the driver's
+// context ID (current_ctx_id), which is never reused within a process.  Every call shares the
+// array and leaves the last call's contents in it; the pipeline clears what
+// must start at zero at the start of each call.  Calls are serialised by a
+// host mutex and each returns only after its GPU work has finished, because
+// two calls whose work overlapped on the GPU would race on the shared array.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -31,9 +36,15 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The array's device address in one context of one device.
+struct DeviceSlot {
+    unsigned long long ctx_id = 0;  // driver context ID the address belongs to (0: none)
+    void *base = nullptr;
+    int sms = 0;
+};
+
 std::mutex g_mu;
-void *g_base[kMaxDevices];  // device address of g_noalloc_scratch, per device
-int g_sms[kMaxDevices];
+DeviceSlot g_slot[kMaxDevices];
 
 bool on_device(const void *p)
 {
@@ -64,35 +75,41 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
     std::lock_guard<std::mutex> lock(g_mu);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FEC_ERR_CUDA;
-    // Set-up on this device's first call: the device address of the array.
-    if (!g_base[dev]) {
+    DeviceSlot &slot = g_slot[dev];
+    // Set-up: the device address of the array in the current context (first
+    // call on this device, or the context changed since).
+    const unsigned long long ctx_id = current_ctx_id();
+    if (!slot.base || ctx_id == 0 || ctx_id != slot.ctx_id) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
             cudaGetLastError();
+            slot = DeviceSlot();
             return FEC_ERR_CUDA;
         }
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms < 1)
+            sms < 1) {
+            slot = DeviceSlot();
             return FEC_ERR_CUDA;
-        g_sms[dev] = sms;
-        g_base[dev] = ptr;
+        }
+        slot.base = ptr;
+        slot.sms = sms;
+        slot.ctx_id = current_ctx_id();  // the lookup made a context current if none was
     }
     Workspace ws;
     ws.device = dev;
-    ws.sms = g_sms[dev];
+    ws.sms = slot.sms;
     {
         Workspace probe;
         probe.sms = ws.sms;
         if (workspace_layout(probe, nullptr, (size_t)kMaxPoints, kSlabCap) > kScratchBytes)
             return FEC_ERR_OOM;  // cannot happen with the constants above; checked anyway
     }
-    workspace_layout(ws, g_base[dev], (size_t)kMaxPoints, kSlabCap);
+    workspace_layout(ws, slot.base, (size_t)kMaxPoints, kSlabCap);
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     Params prm = make_params((uint32_t)n, d);
     if (prm.slab_cap > kSlabCap) prm.slab_cap = kSlabCap;  // wider clouds are rejected on device
-    prm.col_bits = ws.col_bits;
 
     const float *xin = xyz;
     if (!on_device(xyz)) {
@@ -104,29 +121,7 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
     int32_t *lout = dev_out ? labels : ws.labels;
 
     // The same stages as fec_cluster, on the static workspace.
-    const uint32_t un = (uint32_t)n;
-    const bool pk = prm.packed != 0;
-    cudaError_t e = enqueue_front(ws, xin, prm, st);
-    if (e == cudaSuccess)
-        e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
-                        ws.vals_b, false, pk, !pk, ws.sort_status, un, 4, ws.sms, st,
-                        &ws.plan->status, main_sort_source(ws, xin, prm));
-    const int p64 = max_sort_passes(prm);
-    if (e == cudaSuccess && p64 > 4)
-        e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
-                        ws.vals_b, true, pk, !pk, ws.sort_status, un, p64, ws.sms, st,
-                        &ws.plan->status, main_sort_source(ws, xin, prm));
-    if (e == cudaSuccess) e = enqueue_cells(ws, xin, prm, st);
-    if (e == cudaSuccess) e = enqueue_union(ws, prm, min_size, max_size, st);
-    const int kp = kept_sort_passes(un);
-    if (e == cudaSuccess && kp > 0) {
-        e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), ws.sms * 4, st);
-        if (e == cudaSuccess)
-            e = launch_sort(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
-                            ws.kept_key_b(), ws.kept_val_b(), false, false, false,
-                            ws.sort_status, un, kp, ws.sms, st, &ws.plan->status);
-    }
-    if (e == cudaSuccess) e = enqueue_labels(ws, prm, lout, pk, st);
+    cudaError_t e = enqueue_cluster(ws, xin, prm, min_size, max_size, lout, st);
     if (e == cudaSuccess && !dev_out)
         e = cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
     uint32_t status_bits = 0, k = 0;

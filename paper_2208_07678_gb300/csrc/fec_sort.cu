@@ -9,8 +9,9 @@
 // for the main sort), so a pass reads each key and value once and writes them
 // once; with packed payloads the main sort's first pass reads the point
 // coordinates instead and computes each key and payload itself.  Look-back
-// waits are bounded (kWaitCap); a timeout sets ST_WAIT_TIMEOUT and the pass
-// continues with a wrong prefix instead of hanging.  Tile ids are taken from
+// waits are bounded (SortCtl::wait_cap); a timeout sets ST_WAIT_TIMEOUT and
+// the pass finishes with a wrong prefix (every store stays in bounds) instead
+// of hanging; every later kernel of the call then returns at once.  Tile ids are taken from
 // an atomic counter, so a tile only ever waits on tiles already owned by
 // running blocks.
 #include "fec_internal.cuh"
@@ -79,6 +80,8 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     // array for the next pass (which starts only after this one finishes).
     constexpr uint32_t want64 = sizeof(KeyT) == 8 ? 1u : 0u;
     if (ctl->key64 != want64 || (uint32_t)pass >= ctl->npasses) return;
+    if (block_aborted(status)) return;  // an earlier stage gave up
+    const uint32_t wait_cap = ctl->wait_cap;
     const uint32_t par = ctl->parity;
     uint32_t *__restrict__ tstat = tstat_base + (size_t)((pass + par) & 1) * tstride;
     uint32_t *__restrict__ tnext = tstat_base + (size_t)((pass + par + 1) & 1) * tstride;
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
                         if (done) break;
                         uint32_t s = win[j];
                         while ((s & ~kValMask) == 0) {  // not published yet: wait for it
-                            if (++it > kWaitCap) {
+                            if (++it > wait_cap) {
                                 atomicOr(status, ST_WAIT_TIMEOUT);
                                 s = kFlagIncl;
                                 break;
@@ -245,9 +248,11 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
 
 // Digit histograms of every pass for 32-bit keys (count read from ctl).
 __global__ void __launch_bounds__(256) k_hist_u32(SortCtl *__restrict__ ctl,
-                                                   const uint32_t *__restrict__ keys)
+                                                   const uint32_t *__restrict__ keys,
+                                                   const uint32_t *__restrict__ status)
 {
     __shared__ uint32_t h[4][kRadixBins];
+    if (block_aborted(status)) return;
     const uint32_t n = ctl->n;
     const int np = min((int)ctl->npasses, 4);
     for (int i = threadIdx.x; i < 4 * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -271,8 +276,9 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
 {
     const size_t smem = sizeof(SortSmem<KeyT, ValT>);
     static int per_sm = 0;  // resident blocks per SM (persistent grid)
+    static std::atomic<unsigned long long> attr_ctx{0};  // context the attributes were set in
     constexpr bool kXyz = sizeof(ValT) == 8;  // keys from coordinates: packed payloads only
-    if (!per_sm) {
+    if (!per_sm || ctx_setup_needed(attr_ctx)) {
         cudaError_t e = cudaFuncSetAttribute(k_onesweep<KeyT, ValT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -288,6 +294,7 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
                                                                   kSortThreads, smem);
         }
         per_sm = (e != cudaSuccess || a < 1 || b < 1) ? 1 : (a < b ? a : b);
+        ctx_setup_done(attr_ctx);
     }
     grid *= per_sm;
     const int tiles = (int)(((uint64_t)max_n + kSortTile - 1) / kSortTile);
@@ -350,9 +357,10 @@ cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, voi
                                    tile_status, max_n, max_passes, grid, st, status, src);
 }
 
-cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, int grid, cudaStream_t st)
+cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, const uint32_t *status, int grid,
+                            cudaStream_t st)
 {
-    k_hist_u32<<<grid, 256, 0, st>>>(ctl, keys);
+    k_hist_u32<<<grid, 256, 0, st>>>(ctl, keys, status);
     return cudaGetLastError();
 }
 

@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(256, 4)
            uint32_t *__restrict__ nb_first, uint8_t *__restrict__ nb_cnt,
            unsigned long long *__restrict__ edge_set, uint32_t edge_set_size)
 {
+    if (call_aborted(&plan->status)) return;
     // the boundary-edge hash set of k_edges starts empty
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < edge_set_size;
          i += gridDim.x * blockDim.x)
@@ -459,6 +460,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
 {
     extern __shared__ __align__(16) unsigned char region_smem[];
     RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
+    if (block_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -756,8 +758,9 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
 // the giant component's root).  A full probe window falls back to joining.
 __global__ void __launch_bounds__(256)
     k_edges(Plan *plan, const uint2 *__restrict__ edges, uint32_t ecap, uint32_t *parent,
-            unsigned long long *__restrict__ set, uint32_t set_mask)
+            unsigned long long *__restrict__ set, uint32_t set_mask, uint32_t union_cap)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t ne = min(plan->edges_n, ecap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
         const uint2 e = edges[i];
@@ -781,7 +784,7 @@ __global__ void __launch_bounds__(256)
             }
             h = (h + 1) & set_mask;
         }
-        if (first && !uf_unite(parent, ra, rb)) atomicOr(&plan->status, ST_UNION_CAP);
+        if (first && !uf_unite(parent, ra, rb, union_cap)) atomicOr(&plan->status, ST_UNION_CAP);
     }
 }
 
@@ -792,6 +795,7 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
     k_pairs(Plan *plan, Params prm, const SubBox *__restrict__ box, const Rec *__restrict__ rec,
             uint32_t *parent, const uint2 *__restrict__ pairq, uint32_t qcap)
 {
+    if (block_aborted(&plan->status)) return;
     const uint32_t nq = min(plan->pairq_n, qcap);
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -801,13 +805,16 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
     m.T2 = (typename Metric<WIDE>::T)prm.T2;
     m.R1 = prm.R + 1;
     unsigned long long n_same = 0, n_evals = 0;
+    const uint32_t cap = prm.union_cap;
     for (uint32_t base = gw * 32; base < nq; base += nw * 32) {
         const uint32_t i = base + lane;
         uint2 pr = make_uint2(0, 0);
         bool live = false;
         if (i < nq) {
             pr = pairq[i];
-            live = pr.x != 0xffffffffu && uf_find(parent, pr.x) != uf_find(parent, pr.y);
+            bool ok = true;
+            live = pr.x != 0xffffffffu && uf_find(parent, pr.x, cap, ok) != uf_find(parent, pr.y, cap, ok);
+            if (!ok) atomicOr(status, ST_UNION_CAP);
             if (!live) ++n_same;
         }
         uint32_t mask = __ballot_sync(0xffffffffu, live);
@@ -817,7 +824,7 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
             const uint32_t pa = __shfl_sync(0xffffffffu, pr.x, src);
             const uint32_t pb = __shfl_sync(0xffffffffu, pr.y, src);
             if (warp_pair_test<WIDE>(pa, pb, box, rec, m, n_evals) && lane == 0 &&
-                !uf_unite(parent, pa, pb))
+                !uf_unite(parent, pa, pb, cap))
                 atomicOr(status, ST_UNION_CAP);
         }
     }
@@ -834,8 +841,10 @@ constexpr int kFlatSlots = 512;  // per-block table of component sums
 
 __global__ void __launch_bounds__(256, 4)
     k_flatten_stats(Plan *plan, const SubBox *__restrict__ box, const uint32_t *__restrict__ sminidx,
-                    uint32_t *parent, uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin)
+                    uint32_t *parent, uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
+                    uint32_t union_cap)
 {
+    if (block_aborted(&plan->status)) return;
     // Each block takes one contiguous range of sub-cells (a compact piece of
     // space, so few distinct components) and sums sizes and smallest indices
     // per root in a shared-memory table; roots that find no free slot go
@@ -858,11 +867,16 @@ __global__ void __launch_bounds__(256, 4)
         if (valid) {
             // read-only walk: unions are finished, pointers only get shorter
             r = a;
-            for (uint32_t it = 0; it < kUnionCap; ++it) {
+            bool found = false;
+            for (uint32_t it = 0; it <= union_cap; ++it) {
                 const uint32_t p = ld_relaxed(parent + r);
-                if (p == r) break;
+                if (p == r) {
+                    found = true;
+                    break;
+                }
                 r = p;
             }
+            if (!found) atomicOr(&plan->status, ST_UNION_CAP);
             cnt = box[a].count;
             mi = sminidx[a];
             st_relaxed(parent + a, r);
@@ -910,6 +924,7 @@ __global__ void __launch_bounds__(256)
            const uint32_t *__restrict__ cmin, long long min_size, long long max_size,
            uint32_t *__restrict__ kept_key, uint32_t *__restrict__ kept_val)
 {
+    if (block_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -938,6 +953,7 @@ __global__ void __launch_bounds__(256)
     k_rank(Plan *plan, const uint32_t *__restrict__ va, const uint32_t *__restrict__ vb,
            int32_t *__restrict__ crank)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t k = plan->kept.n;
     const uint32_t *__restrict__ v = (plan->kept.npasses & 1u) ? vb : va;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
@@ -951,6 +967,7 @@ __global__ void __launch_bounds__(256)
     k_sclabel(Plan *plan, const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
               int32_t *__restrict__ sclab, int32_t *__restrict__ labels, uint32_t n)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x)
         sclab[a] = crank[parent[a]];
@@ -971,6 +988,7 @@ __global__ void __launch_bounds__(256)
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
              const int32_t *__restrict__ sclab, int32_t *__restrict__ labels)
 {
+    if (call_aborted(&plan->status)) return;
     const uint32_t n = plan->sort.n;
     const uint32_t *__restrict__ idx = (plan->sort.npasses & 1u) ? idx_b : idx_a;
     const uint32_t n8 = n / 8;
@@ -1032,11 +1050,11 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     const uint32_t ecap = (uint32_t)ws.edges_cap;
     const bool wide = prm.R + 1 > 26754;
     const size_t smem = sizeof(RegionSmem);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_ctx{0};  // context the attributes were set in
+    if (ctx_setup_needed(attr_ctx)) {
         cudaFuncSetAttribute(k_region<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_region<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        ctx_setup_done(attr_ctx);
     }
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item (cell, sub-cell, edge) per thread
     k_nbrs<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
@@ -1055,7 +1073,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
     k_edges<<<grid1, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
-                                        (uint32_t)(ws.edge_set_size - 1));
+                                        (uint32_t)(ws.edge_set_size - 1), prm.union_cap);
     FEC_MARK(ws, "k_edges", st);
     if (!wide)
         k_pairs<false><<<grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
@@ -1065,7 +1083,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
                                                             ws.pairq, qcap);
     FEC_MARK(ws, "k_pairs", st);
     k_flatten_stats<<<grid1, 256, 0, st>>>(ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
-                                                 ws.cmin);
+                                                 ws.cmin, prm.union_cap);
     FEC_MARK(ws, "k_flatten_stats", st);
     k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, min_size, max_size,
                                         ws.kept_key_a(), ws.kept_val_a());

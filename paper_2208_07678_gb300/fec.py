@@ -5,7 +5,7 @@ library.  There is no CPU fallback; if the library is missing this module
 raises on first use.  Functions keep the C names (``fec_create``,
 ``fec_cluster``, ``fec_cluster_batch``, ``fec_serve_submit``,
 ``fec_serve_poll``, ``fec_serve_poll_timed``, ``fec_get_stats``, ``fec_workspace_bytes``,
-``fec_status_string``, ``fec_destroy``) and take raw pointers like the C ABI;
+``fec_set_iteration_caps``, ``fec_status_string``, ``fec_destroy``) and take raw pointers like the C ABI;
 ``Context`` adds array conveniences on top (numpy arrays = host memory,
 torch CUDA tensors = device memory).
 """
@@ -29,8 +29,10 @@ FEC_OK, FEC_ERR_NOT_READY, FEC_ERR_TIMEOUT = 0, 7, 9
 # Every function the header declares (checked by the CPU tests against include/fec.h).
 EXPORTS = ("fec_create", "fec_destroy", "fec_cluster", "fec_cluster_batch", "fec_serve_submit",
            "fec_serve_poll", "fec_serve_poll_timed", "fec_get_stats", "fec_workspace_bytes", "fec_status_string",
-           "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc")
+           "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc", "fec_set_iteration_caps")
 FEC_NOALLOC_MAX_POINTS = 32768
+FEC_DEFAULT_WAIT_CAP = 1 << 22
+FEC_DEFAULT_UNION_CAP = 1 << 20
 
 
 class FecError(RuntimeError):
@@ -106,6 +108,8 @@ def load(build_if_missing: bool = False):
     lib.fec_trace_read.restype = ctypes.c_int
     lib.fec_cluster_noalloc.argtypes = [f32p, i64, ctypes.c_float, i64, i64, vp, i32p, vp]
     lib.fec_cluster_noalloc.restype = ctypes.c_int
+    lib.fec_set_iteration_caps.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+    lib.fec_set_iteration_caps.restype = ctypes.c_int
     lib.fec_status_string.argtypes = [ctypes.c_int]
     lib.fec_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -198,6 +202,10 @@ def fec_trace_read(ctx) -> list:
     n = lib.fec_trace_read(ctx, buf, n)
     return [{"name": e.name.decode(), "launches": int(e.launches), "total_ms": float(e.total_ms)}
             for e in buf[:n]]
+
+
+def fec_set_iteration_caps(ctx, wait_cap: int, union_cap: int) -> int:
+    return load().fec_set_iteration_caps(ctx, int(wait_cap), int(union_cap))
 
 
 def fec_workspace_bytes(n: int, d: float) -> int:
@@ -313,3 +321,8 @@ class Context:
 
     def trace_read(self) -> list:
         return fec_trace_read(self.handle)
+
+    def set_iteration_caps(self, wait_cap=FEC_DEFAULT_WAIT_CAP, union_cap=FEC_DEFAULT_UNION_CAP):
+        st = fec_set_iteration_caps(self.handle, wait_cap, union_cap)
+        if st != FEC_OK:
+            raise FecError(st, "fec_set_iteration_caps")

@@ -73,3 +73,81 @@ def test_noalloc_rejects_clouds_above_its_capacity():
     lab = np.zeros(n, np.int32)
     st, _ = fec.fec_cluster_noalloc(x.ctypes.data, n, 0.5, 1, 10, lab.ctypes.data)
     assert fec.STATUS[st] == "FEC_ERR_INVALID_ARG"
+
+
+def test_noalloc_reports_a_cloud_wider_than_its_slab_index():
+    """The static workspace indexes at most 65,536 grid cells along the major
+    axis: a cloud wider than that is refused with FEC_ERR_OUT_OF_RANGE (the
+    device plan sees the overflow before any key is sorted), and the next
+    call on an ordinary cloud is exact again."""
+    import torch
+
+    from paper_2208_07678_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    d = 0.05  # cells of 52 units: 65,536 of them span about 3,328 m
+    x = np.array([[0.0, 0.0, 0.0], [3500.0, 0.0, 0.0], [3500.0, 0.03125, 0.0]], np.float32)
+    lab = np.full(3, -7, np.int32)
+    st, _ = fec.fec_cluster_noalloc(x.ctypes.data, 3, d, 1, fec.INT64_MAX, lab.ctypes.data)
+    assert fec.STATUS[st] == "FEC_ERR_OUT_OF_RANGE"
+    with fec.Context(device=0) as ctx:
+        want, kw = ctx.cluster(x, d, 1, fec.INT64_MAX)
+    assert kw == 2  # fec_cluster has no such limit
+    c = synth.blobs_20k()
+    ref = _reference([c])[0]
+    st, k, lab = _noalloc(c, False)
+    assert fec.STATUS[st] == "FEC_OK" and k == ref[1]
+    np.testing.assert_array_equal(lab, ref[0])
+
+
+def test_noalloc_reports_boundary_lists_it_cannot_hold():
+    """A lattice with one point in every sub-cell (32^3 points, spacing h =
+    0.25 m at d = 0.5 m) makes far more joined sub-cell pairs across the
+    neighbour step's regions than the fixed lists hold (two entries per
+    point).  fec_cluster grows its lists and retries; the static workspace
+    cannot, so the call reports FEC_ERR_OOM.  The next ordinary call is exact."""
+    import torch
+
+    torch.cuda.set_device(0)
+    g = (np.arange(32, dtype=np.float32) + 0.5) * 0.25
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    x = np.ascontiguousarray(x[np.random.default_rng(5).permutation(len(x))])
+    n = len(x)
+    assert n <= fec.FEC_NOALLOC_MAX_POINTS
+    with fec.Context(device=0) as ctx:
+        want, kw = ctx.cluster(x, 0.5, 1, fec.INT64_MAX)
+    assert kw == 1 and np.all(want == 0)
+    lab = np.full(n, -7, np.int32)
+    st, _ = fec.fec_cluster_noalloc(x.ctypes.data, n, 0.5, 1, fec.INT64_MAX, lab.ctypes.data)
+    assert fec.STATUS[st] == "FEC_ERR_OOM"
+    c = synth.blobs_20k()
+    ref = _reference([c])[0]
+    st, k, lab = _noalloc(c, True)
+    assert fec.STATUS[st] == "FEC_OK" and k == ref[1]
+    np.testing.assert_array_equal(lab, ref[0])
+
+
+def test_noalloc_after_device_reset(tmp_path):
+    """The cached workspace address belongs to the context it was taken in.
+    A separate process (sharing the library's CUDA runtime: it links the
+    library's objects) calls the entry point, resets the device, and calls it
+    again: the second call must redo its set-up in the new context and give
+    the same labels.  Run once, on a 4,000-point cloud."""
+    import glob
+    import os
+    import subprocess
+
+    from paper_2208_07678_gb300 import build as libbuild
+
+    libbuild.build()
+    here = os.path.dirname(os.path.abspath(__file__))
+    objs = sorted(glob.glob(os.path.join(libbuild.BUILD, "*.o")))
+    exe = str(tmp_path / "noalloc_reset")
+    cmd = [libbuild.nvcc(), *libbuild.ARCH, "-O2", "-std=c++17", "-I", libbuild.INCLUDE,
+           os.path.join(here, "noalloc_reset.cu"), *objs, "-lpthread", "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "labels equal" in r.stdout
