@@ -110,9 +110,16 @@ fec_status fec_cluster(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64
 /* Cluster nb independent frames in one device pass (frames of uneven size,
  * per-frame d and size bounds).  Frame f holds points offsets[f] ..
  * offsets[f+1]-1 of the concatenated xyz.  Labels are frame-local (each frame
- * numbered 0..k_f-1 exactly as fec_cluster would number it alone).
+ * numbered 0..k_f-1 exactly as fec_cluster would number it alone).  Frames
+ * that share a radius run together as one pass of the pipeline (a sort
+ * segmented by frame, a cell table and size filter per frame), radius groups
+ * run concurrently, and the whole batch is captured into a CUDA graph that is
+ * replayed for later batches of the same shape (offsets, radii, bounds and
+ * buffers); the launch configuration is tuned on the first batch of a shape
+ * (see fec_options.autotune_cache).
  *   xyz          float32 [offsets[nb]][3], host or device.
- *   offsets      host int64 [nb+1], offsets[0] = 0, non-decreasing.
+ *   offsets      host int64 [nb+1], offsets[0] = 0, non-decreasing,
+ *                offsets[nb] <= FEC_MAX_POINTS.
  *   d, min_size, max_size  host arrays [nb].
  *   labels       int32 [offsets[nb]], host or device.
  *   num_clusters host int32 [nb].

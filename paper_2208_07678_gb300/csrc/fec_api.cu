@@ -50,6 +50,10 @@ Params make_params(uint32_t n, float d)
     while (((int64_t)1 << lg) < (int64_t)p.S) ++lg;
     p.div_s = 24 + lg;
     p.div_m = (uint32_t)((((uint64_t)1 << p.div_s) + (uint64_t)p.S - 1) / (uint64_t)p.S);
+    // one frame (a single cloud) unless the caller lays out several
+    p.nf = 1;
+    p.ntiles = frame_tiles(n);
+    p.rows = n;
     return p;
 }
 
@@ -81,7 +85,7 @@ int kept_sort_passes(uint32_t n)
 // Workspace
 // ---------------------------------------------------------------------------
 
-size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap)
+size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap, uint32_t nf_cap)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) -> void * {
@@ -91,14 +95,17 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
         return p;
     };
     const size_t n = cap_n;
+    if (nf_cap < 1) nf_cap = 1;
     ws.plan = (Plan *)take(sizeof(Plan));
+    ws.frames = (Frame *)take(sizeof(Frame) * nf_cap);
+    ws.fhist = (uint32_t *)take(4 * (size_t)nf_cap * kMaxPasses * kRadixBins);
     ws.xyz = (float *)take(12 * n);
     ws.labels = (int32_t *)take(4 * n);
     ws.keys_a = take(8 * n);
     ws.keys_b = take(8 * n);
     ws.vals_a = take(8 * n);
     ws.vals_b = take(8 * n);
-    ws.sort_status = (uint32_t *)take(4 * sort_status_words((uint32_t)n));
+    ws.sort_status = (uint32_t *)take(4 * sort_status_words(max_tiles(n, nf_cap)));
     ws.scan_status = (unsigned long long *)take(8 * (n / kScanTile + 2));
     ws.rec = (Rec *)take(sizeof(Rec) * n);
     ws.sc_of = (uint32_t *)take(4 * n);
@@ -114,6 +121,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     ws.big = (uint32_t *)take(4 * n);
     ws.cell_key = (unsigned long long *)take(8 * n);
     ws.cell_sc = (uint32_t *)take(4 * (n + 2));
+    ws.cframe = (uint32_t *)take(4 * n);
     ws.slab_lo = (uint32_t *)take(4 * (size_t)slab_cap);
     ws.slab_hi = (uint32_t *)take(4 * (size_t)slab_cap);
     const size_t lists = 2 * n * (size_t)(ws.list_scale ? ws.list_scale : 1);
@@ -142,6 +150,7 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
         ws.bytes = off;
         ws.cap_n = cap_n;
         ws.slab_cap = slab_cap;
+        ws.nf_cap = nf_cap;
     }
     return off;
 }
@@ -151,43 +160,43 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
 // ---------------------------------------------------------------------------
 
 cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm_in,
-                            long long min_size, long long max_size, int32_t *labels,
-                            cudaStream_t st)
+                            const FrontArgs &fa, int32_t *labels, bool fill_labels, cudaStream_t st)
 {
     Params prm = prm_in;
     prm.col_bits = ws.col_bits;
     const uint32_t n = prm.n;
     const int sort_grid = ws.sms;  // per SM; the sort multiplies by its occupancy
-    cudaError_t e = enqueue_front(ws, xyz, prm, st);
+    cudaError_t e = enqueue_front(ws, xyz, prm, fa, st);
     if (e != cudaSuccess) return e;
     // a2: both key widths are enqueued; the plan enables one of them.
     const bool pk = prm.packed != 0;
     e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b, ws.vals_b,
-                    false, pk, !pk, ws.sort_status, n, 4, sort_grid, st, &ws.plan->status,
+                    false, pk, !pk, ws.sort_status, prm.ntiles, 4, sort_grid, st, &ws.plan->status,
                     main_sort_source(ws, xyz, prm));
     if (e != cudaSuccess) return e;
     const int p64 = max_sort_passes(prm);
     if (p64 > 4) {
         e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
-                        ws.vals_b, true, pk, !pk, ws.sort_status, n, p64, sort_grid, st,
+                        ws.vals_b, true, pk, !pk, ws.sort_status, prm.ntiles, p64, sort_grid, st,
                         &ws.plan->status, main_sort_source(ws, xyz, prm));
         if (e != cudaSuccess) return e;
     }
     e = enqueue_cells(ws, xyz, prm, st);
     if (e != cudaSuccess) return e;
-    e = enqueue_union(ws, prm, min_size, max_size, st);
+    e = enqueue_union(ws, prm, st);
     if (e != cudaSuccess) return e;
-    const int kp = kept_sort_passes(n);
+    // kept components by their smallest input row (rows < prm.rows)
+    const int kp = kept_sort_passes(prm.rows);
     if (kp > 0) {
         e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), &ws.plan->status, ws.sms * 4, st);
         if (e != cudaSuccess) return e;
         FEC_MARK(ws, "hist_kept", st);
         e = launch_sort(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
-                        ws.kept_key_b(), ws.kept_val_b(), false, false, false, ws.sort_status, n,
-                        kp, sort_grid, st, &ws.plan->status);
+                        ws.kept_key_b(), ws.kept_val_b(), false, false, false, ws.sort_status,
+                        frame_tiles(n), kp, sort_grid, st, &ws.plan->status);
         if (e != cudaSuccess) return e;
     }
-    return enqueue_labels(ws, prm, labels, prm.packed != 0, st);
+    return enqueue_labels(ws, prm, labels, fill_labels, st);
 }
 
 // Small summary of a finished call, packed on the device for one copy.
@@ -492,7 +501,11 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
     }
     const bool dev_out = is_device_ptr(labels);
     int32_t *lout = dev_out ? labels : ws.labels;
-    if (enqueue_cluster(ws, xin, prm, min_size, max_size, lout, ctx->stream) != cudaSuccess)
+    FrontArgs fa;
+    fa.single = true;
+    fa.min_size = min_size;
+    fa.max_size = max_size;
+    if (enqueue_cluster(ws, xin, prm, fa, lout, true, ctx->stream) != cudaSuccess)
         return FEC_ERR_CUDA;
     if (!dev_out) {
         if (cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost,
@@ -650,6 +663,7 @@ fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offs
         if (s != FEC_OK) return s;
     }
     if (offsets[nb] > 0 && (!xyz || !labels)) return FEC_ERR_INVALID_ARG;
+    if (offsets[nb] > FEC_MAX_POINTS) return FEC_ERR_INVALID_ARG;  // rows must fit 32 bits
     std::lock_guard<std::mutex> lock(ctx->mu);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FEC_ERR_CUDA;
     if (offsets[nb] == 0) {

@@ -8,6 +8,8 @@
 // cell is split into 2x2x2 sub-cells of side h; since 3(h-1)^2 <= T2, all
 // points of one sub-cell are pairwise within d, so a sub-cell is a clique and
 // becomes one union-find node.
+#include <algorithm>
+
 #include "fec_internal.cuh"
 
 namespace fec {
@@ -33,98 +35,79 @@ __device__ __forceinline__ T warp_max(T v)
 
 }  // namespace
 
-// Reset the plan for a call of n points.
-__global__ void k_init(Plan *plan, uint32_t n, uint32_t kept_passes, uint32_t wait_cap)
+// Reset the plan and the frame table for a call of n points in nf frames
+// (one block does the plan; every block clears its share of the frames'
+// device fields and per-frame histograms).  A single cloud (single = 1)
+// also gets its one frame's static fields here, so it needs no upload.
+__global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint32_t n,
+                       uint32_t kept_passes, uint32_t wait_cap, int single, long long min_size,
+                       long long max_size)
 {
     const int t = threadIdx.x;
-    if (t < 3) {
-        plan->lo[t] = INT32_MAX;
-        plan->hi[t] = INT32_MIN;
-        plan->perm[t] = t;
-        plan->bits[t] = 0;
+    if (blockIdx.x == 0) {
+        if (t < 3) {
+            plan->perm[t] = t;
+            plan->bits[t] = 0;
+        }
+        if (t == 0) {
+            plan->key_bits = 0;
+            plan->status = 0;
+            plan->M_s = 0;
+            plan->M_c = 0;
+            plan->n_big = 0;
+            plan->n_huge = 0;
+            plan->scan_tile_counter = 0;
+            plan->pairq_n = 0;
+            plan->use_cols = 0;
+            plan->edges_n = 0;
+            plan->region_counter = 0;
+            plan->slab_need = 0;
+            plan->sort.n = n;
+            plan->sort.npasses = 0;
+            plan->sort.key64 = 0;
+            plan->sort.parity = 0;
+            plan->sort.wait_cap = wait_cap;
+            plan->kept.wait_cap = wait_cap;
+            plan->kept.n = 0;
+            plan->kept.npasses = kept_passes;
+            plan->kept.key64 = 0;
+            plan->kept.parity = 0;
+        }
+        for (int i = t; i < kMaxPasses * kRadixBins; i += blockDim.x) (&plan->kept.hist[0][0])[i] = 0;
+        if (t < 8) plan->ctr[t] = 0;
+        if (t < kMaxPasses) {
+            plan->sort.tile_counter[t] = 0;
+            plan->kept.tile_counter[t] = 0;
+        }
     }
-    if (t == 0) {
-        plan->key_bits = 0;
-        plan->status = 0;
-        plan->M_s = 0;
-        plan->M_c = 0;
-        plan->n_big = 0;
-        plan->n_huge = 0;
-        plan->scan_tile_counter = 0;
-        plan->pairq_n = 0;
-        plan->use_cols = 0;
-        plan->edges_n = 0;
-        plan->region_counter = 0;
-        plan->sort.n = n;
-        plan->sort.npasses = 0;
-        plan->sort.key64 = 0;
-        plan->sort.parity = 0;
-        plan->sort.wait_cap = wait_cap;
-        plan->kept.wait_cap = wait_cap;
-        plan->kept.n = 0;
-        plan->kept.npasses = kept_passes;
-        plan->kept.key64 = 0;
-        plan->kept.parity = 0;
+    const uint32_t gt = blockIdx.x * blockDim.x + t, gs = gridDim.x * blockDim.x;
+    for (uint32_t f = gt; f < nf; f += gs) {
+        Frame &F = fr[f];
+        if (single) {
+            F.in_off = 0;
+            F.pos_off = 0;
+            F.n = n;
+            F.tile0 = 0;
+            F.min_size = min_size;
+            F.max_size = max_size;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            F.lo[a] = INT32_MAX;
+            F.hi[a] = INT32_MIN;
+        }
+        F.kept = 0;
+        F.nslab = 0;
+        F.slab_base = 0;
     }
-    for (int i = t; i < kMaxPasses * kRadixBins; i += blockDim.x) {
-        (&plan->sort.hist[0][0])[i] = 0;
-        (&plan->kept.hist[0][0])[i] = 0;
-    }
-    if (t < 8) plan->ctr[t] = 0;
-    if (t < kMaxPasses) {
-        plan->sort.tile_counter[t] = 0;
-        plan->kept.tile_counter[t] = 0;
-    }
+    const size_t hw = (size_t)nf * kMaxPasses * kRadixBins;
+    for (size_t i = gt; i < hw; i += gs) fhist[i] = 0;
 }
 
-// a1: validate and quantise every coordinate, reduce the bounding box of q.
-__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, uint32_t n, Plan *plan)
+// Block-wide min / max of three values per thread into s (thread 0 reads).
+__device__ __forceinline__ void block_box(int32_t lo[3], int32_t hi[3], int32_t (*s_lo)[8],
+                                          int32_t (*s_hi)[8])
 {
-    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
-    int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
-    uint32_t st = 0;
-    // Four consecutive points (48 bytes: three 16-byte loads when aligned)
-    // per thread and step.
-    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
-    const uint32_t ngroups = (n + 3) / 4;
-    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngroups;
-         gi += gridDim.x * blockDim.x) {
-        const uint32_t i0 = gi * 4;
-        const uint32_t cnt = min(4u, n - i0);
-        float f[12];
-        if (vec && cnt == 4) {
-            const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * (size_t)gi;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const float4 v = __ldcs(src + t);
-                f[4 * t + 0] = v.x;
-                f[4 * t + 1] = v.y;
-                f[4 * t + 2] = v.z;
-                f[4 * t + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < 12; ++t)
-                f[t] = (uint32_t)t < 3 * cnt ? __ldcs(xyz + 3 * (size_t)i0 + t) : 0.0f;
-        }
-#pragma unroll
-        for (int t = 0; t < 12; ++t) {
-            if ((uint32_t)t >= 3 * cnt) break;
-            const int a = t % 3;
-            int32_t q;
-            const int e = quantize1(f[t], q);
-            if (e == 1) st |= ST_NONFINITE;
-            else if (e == 2) st |= ST_OUT_OF_RANGE;
-            else {
-                lo[a] = min(lo[a], q);
-                hi[a] = max(hi[a], q);
-            }
-        }
-    }
-    __shared__ int32_t s_lo[3][8], s_hi[3][8];
-    __shared__ uint32_t s_st;
-    if (threadIdx.x == 0) s_st = 0;
-    __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -134,7 +117,6 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, uin
             s_hi[a][w] = vh;
         }
     }
-    if (st) atomicOr(&s_st, st);
     __syncthreads();
     if (threadIdx.x < 3) {
         const int a = threadIdx.x;
@@ -143,57 +125,219 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, uin
             vl = min(vl, s_lo[a][k]);
             vh = max(vh, s_hi[a][k]);
         }
-        if (vl != INT32_MAX) {
-            atomicMin(&plan->lo[a], vl);
-            atomicMax(&plan->hi[a], vh);
+        s_lo[a][0] = vl;
+        s_hi[a][0] = vh;
+    }
+    __syncthreads();
+}
+
+// Work units of the bounding-box and key kernels: each sort tile (which never
+// straddles two frames) split into kUnitsPerTile chunks.  Unit u covers
+// frame-local indices [first, first + count) of frame f (count may be 0).
+constexpr uint32_t kUnitsPerTile = 5;
+constexpr uint32_t kUnit = kSortTile / kUnitsPerTile;  // 1024 points
+static_assert(kUnit * kUnitsPerTile == kSortTile, "units split a tile evenly");
+struct TileSpan {
+    uint32_t f, first, count;
+};
+__device__ __forceinline__ TileSpan unit_span(const Frame *__restrict__ fr, uint32_t nf, uint32_t u)
+{
+    const uint32_t t = u / kUnitsPerTile;
+    TileSpan sp;
+    sp.f = frame_of_tile(fr, nf, t);
+    sp.first = (t - fr[sp.f].tile0) * (uint32_t)kSortTile + (u - t * kUnitsPerTile) * kUnit;
+    const uint32_t n = fr[sp.f].n;
+    sp.count = sp.first < n ? min(kUnit, n - sp.first) : 0u;
+    return sp;
+}
+// The units block b takes: with several frames a contiguous share
+// [lo, hi) of the call's units (so that its units mostly belong to one
+// frame), with one frame every gridDim.x-th unit from blockIdx.x (the whole
+// grid then sweeps the input in order).
+struct UnitRange {
+    uint32_t lo, hi, step;
+};
+__device__ __forceinline__ UnitRange block_units(uint32_t ntiles, uint32_t nf)
+{
+    const uint64_t U = (uint64_t)ntiles * kUnitsPerTile;
+    if (nf == 1) return UnitRange{blockIdx.x, (uint32_t)U, gridDim.x};
+    return UnitRange{(uint32_t)(U * blockIdx.x / gridDim.x), (uint32_t)(U * (blockIdx.x + 1) / gridDim.x), 1u};
+}
+
+// Twelve floats (four points) of rows [row, row + cnt) of xyz: three 16-byte
+// loads when the rows are aligned and complete.
+__device__ __forceinline__ void load_rows4(const float *__restrict__ xyz, uint32_t row, uint32_t cnt,
+                                           bool vec, float f[12])
+{
+    if (vec && cnt == 4) {
+        const float4 *src = reinterpret_cast<const float4 *>(xyz + 3 * (size_t)row);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const float4 v = __ldcs(src + t);
+            f[4 * t + 0] = v.x;
+            f[4 * t + 1] = v.y;
+            f[4 * t + 2] = v.z;
+            f[4 * t + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < 12; ++t) f[t] = (uint32_t)t < 3 * cnt ? __ldcs(xyz + 3 * (size_t)row + t) : 0.0f;
+    }
+}
+
+// a1: validate and quantise every coordinate, reduce each frame's bounding
+// box of q.  A block keeps its partial box until one of its units belongs
+// to another frame (a single cloud: once, at the end).
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, Plan *plan,
+                                              Frame *__restrict__ fr, Params prm)
+{
+    __shared__ int32_t s_lo[3][8], s_hi[3][8];
+    __shared__ uint32_t s_st;
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
+    int32_t hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    uint32_t st = 0;
+    if (threadIdx.x == 0) s_st = 0;
+    uint32_t cur = 0xffffffffu;  // frame of the partial box (block-uniform)
+    auto flush = [&]() {
+        block_box(lo, hi, s_lo, s_hi);
+        if (threadIdx.x < 3 && s_lo[threadIdx.x][0] != INT32_MAX) {
+            atomicMin(&fr[cur].lo[threadIdx.x], s_lo[threadIdx.x][0]);
+            atomicMax(&fr[cur].hi[threadIdx.x], s_hi[threadIdx.x][0]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = INT32_MAX;
+            hi[a] = INT32_MIN;
+        }
+        __syncthreads();
+    };
+    // groups of four rows [row0 + 4 g0, row0 + count), every gstep-th
+    auto rows = [&](uint32_t row0, uint32_t count, uint32_t g0, uint32_t gstep) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(xyz) & 15) == 0) && (row0 & 3u) == 0;
+        for (uint32_t gi = g0; 4 * gi < count; gi += gstep) {
+            const uint32_t cnt = min(4u, count - 4 * gi);
+            float f[12];
+            load_rows4(xyz, row0 + 4 * gi, cnt, vec, f);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                if ((uint32_t)k >= 3 * cnt) break;
+                const int a = k % 3;
+                int32_t q;
+                const int e = quantize1(f[k], q);
+                if (e == 1) st |= ST_NONFINITE;
+                else if (e == 2) st |= ST_OUT_OF_RANGE;
+                else {
+                    lo[a] = min(lo[a], q);
+                    hi[a] = max(hi[a], q);
+                }
+            }
+        }
+    };
+    if (!MULTI) {  // one frame: the whole grid sweeps its rows
+        cur = 0;
+        rows(fr[0].in_off, prm.n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    } else {
+        const UnitRange ur = block_units(prm.ntiles, prm.nf);
+        for (uint32_t u = ur.lo; u < ur.hi; u += ur.step) {
+            const TileSpan sp = unit_span(fr, prm.nf, u);
+            if (sp.f != cur) {
+                if (cur != 0xffffffffu) flush();
+                cur = sp.f;
+            }
+            rows(fr[sp.f].in_off + sp.first, sp.count, threadIdx.x, blockDim.x);
         }
     }
+    if (cur != 0xffffffffu) flush();
+    if (st) atomicOr(&s_st, st);
+    __syncthreads();
     if (threadIdx.x == 0 && s_st) atomicOr(&plan->status, s_st);
 }
 
 // a1: choose the axis order (largest cell extent major, smallest minor) and
-// the key layout; disable the rest of the pipeline on a data error.
-__global__ void k_plan(Plan *plan, Params prm)
+// the key layout, the same for every frame of the call (from the largest
+// extent per axis over the frames); lay out each frame's part of the slab
+// index; disable the rest of the pipeline on a data error.  One block.
+__global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr, Params prm)
 {
-    if (threadIdx.x != 0) return;
-    if (plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) {
-        plan->sort.n = 0;
+    __shared__ uint32_t s_cm[3];
+    __shared__ uint32_t s_scan[256];
+    __shared__ int s_perm0;
+    __shared__ uint32_t s_stop;
+    const int t = threadIdx.x;
+    if (t < 3) s_cm[t] = 0;
+    if (t == 0) s_stop = (plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) ? 1u : 0u;
+    __syncthreads();
+    if (s_stop) {
+        if (t == 0) plan->sort.n = 0;
         return;
     }
-    uint32_t cm[3];
-    for (int a = 0; a < 3; ++a) {
-        const int64_t ext = (int64_t)plan->hi[a] - plan->lo[a];
-        cm[a] = (uint32_t)(ext / prm.S);
+    for (uint32_t f = t; f < prm.nf; f += blockDim.x)
+        for (int a = 0; a < 3; ++a)
+            atomicMax(&s_cm[a], (uint32_t)(((int64_t)fr[f].hi[a] - fr[f].lo[a]) / prm.S));
+    __syncthreads();
+    if (t == 0) {
+        uint32_t cm[3] = {s_cm[0], s_cm[1], s_cm[2]};
+        int perm[3] = {0, 1, 2};
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j)
+                if (cm[perm[j]] > cm[perm[i]]) {
+                    int tt = perm[i];
+                    perm[i] = perm[j];
+                    perm[j] = tt;
+                }
+        uint32_t total = 0;
+        for (int p = 0; p < 3; ++p) {
+            plan->perm[p] = perm[p];
+            plan->bits[p] = bitlen(cm[perm[p]]);
+            total += plan->bits[p];
+        }
+        s_perm0 = perm[0];
+        if (total > 61) {
+            plan->status |= ST_KEY_OVERFLOW;
+            plan->sort.n = 0;
+            s_stop = 1;
+        } else {
+            plan->key_bits = total + 3;
+            plan->use_cols =
+                (prm.nf == 1 && plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
+            plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
+            plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
+            plan->kept.parity = plan->sort.npasses & 1u;  // the look-back array the main sort leaves clear
+        }
     }
-    int perm[3] = {0, 1, 2};
-    for (int i = 0; i < 3; ++i)
-        for (int j = i + 1; j < 3; ++j)
-            if (cm[perm[j]] > cm[perm[i]]) {
-                int t = perm[i];
-                perm[i] = perm[j];
-                perm[j] = t;
-            }
-    uint32_t total = 0;
-    for (int p = 0; p < 3; ++p) {
-        plan->perm[p] = perm[p];
-        plan->bits[p] = bitlen(cm[perm[p]]);
-        total += plan->bits[p];
+    __syncthreads();
+    if (s_stop) return;
+    // each frame's slab entries (its major cell coordinates), laid out in
+    // frame order: an exclusive scan in chunks of 256 frames
+    const int p0 = s_perm0;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < prm.nf; c0 += blockDim.x) {
+        const uint32_t f = c0 + t;
+        uint32_t ns = 0;
+        if (f < prm.nf) ns = (uint32_t)(((int64_t)fr[f].hi[p0] - fr[f].lo[p0]) / prm.S) + 1u;
+        s_scan[t] = ns;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+            const uint32_t v = t >= o ? s_scan[t - o] : 0u;
+            __syncthreads();
+            s_scan[t] += v;
+            __syncthreads();
+        }
+        if (f < prm.nf) {
+            fr[f].nslab = ns;
+            fr[f].slab_base = carry + s_scan[t] - ns;
+        }
+        carry += s_scan[255];
+        __syncthreads();
     }
-    if (total > 61) {
-        plan->status |= ST_KEY_OVERFLOW;
-        plan->sort.n = 0;
-        return;
+    if (t == 0) {
+        plan->slab_need = carry;
+        if (carry > prm.slab_cap) {  // the host grows the slab index and runs the call again
+            plan->status |= ST_SIZE_OVERFLOW;
+            plan->sort.n = 0;
+        }
     }
-    if (cm[perm[0]] + 1 > prm.slab_cap) {  // cannot happen for |q| < 2^23
-        plan->status |= ST_SIZE_OVERFLOW;
-        plan->sort.n = 0;
-        return;
-    }
-    plan->key_bits = total + 3;
-    plan->use_cols = (plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
-    plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
-    plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
-    plan->kept.parity = plan->sort.npasses & 1u;  // the look-back array the main sort leaves clear
 }
 
 // Arrays zeroed by the key kernel for the later stages.
@@ -207,19 +351,20 @@ struct Clears {
     size_t max_words;
 };
 
-// a1: grid keys of all points, plus the digit histograms of every radix pass.
-// With STORE false only the histograms are made: the sort's first pass then
-// computes the keys and payloads again from the coordinates it reads, which
-// saves writing and re-reading them (packed layout only).
-template <typename KeyT, bool PACKED, bool STORE>
+// a1: grid keys of all points, plus each frame's digit histograms of every
+// radix pass.  With STORE false only the histograms are made: the sort's
+// first pass then computes the keys and payloads again from the coordinates
+// it reads, which saves writing and re-reading them (packed layout only).
+// A block's shared-memory histograms go to the frame's global ones when one
+// of its units belongs to another frame.
+template <typename KeyT, bool STORE, bool MULTI>
 __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *plan, const Params &prm,
-                                          KeyT *__restrict__ keys,
-                                          unsigned long long *__restrict__ vals, const Clears &clr,
+                                          const Frame *__restrict__ fr, uint32_t *__restrict__ fhist,
+                                          KeyT *__restrict__ keys, const Clears &clr,
                                           uint32_t (*h)[kRadixBins])
 {
     SortCtl *ctl = &plan->sort;
-    const uint32_t n = ctl->n;
-    if (n == 0) return;
+    if (ctl->n == 0) return;
     // arrays the later stages need zeroed (in place of separate memsets)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < clr.max_words;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -233,89 +378,91 @@ __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *p
     const int np = (int)ctl->npasses;
     for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
     GridMap g;
-    g.load(plan, prm);
+    g.load(plan, prm, fr[0]);
     __syncthreads();
-    // Four consecutive points per thread and step: three 16-byte loads of
-    // their coordinates when aligned, vector stores of keys and payloads.
-    const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
-    const uint32_t ngroups = (n + 3) / 4;
-    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ngroups;
-         gi += gridDim.x * blockDim.x) {
-        const uint32_t i0 = gi * 4;
-        const uint32_t cnt = min(4u, n - i0);
-        float f[12];
-        if (vec && cnt == 4) {
-            const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * (size_t)gi;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const float4 v = __ldcs(src + t);
-                f[4 * t + 0] = v.x;
-                f[4 * t + 1] = v.y;
-                f[4 * t + 2] = v.z;
-                f[4 * t + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < 12; ++t)
-                f[t] = (uint32_t)t < 3 * cnt ? __ldcs(xyz + 3 * (size_t)i0 + t) : 0.0f;
+    uint32_t cur = 0xffffffffu;  // frame whose counts are in h (block-uniform)
+    auto flush = [&]() {
+        __syncthreads();
+        uint32_t *dst = fhist + (size_t)cur * kMaxPasses * kRadixBins;
+        for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {
+            const uint32_t v = (&h[0][0])[i];
+            if (v) atomicAdd(dst + i, v);
+            (&h[0][0])[i] = 0;
         }
-        KeyT k[4];
-        unsigned long long v[4];
+        __syncthreads();
+    };
+    // four consecutive points per thread and step: groups of four rows
+    // [row0 + 4 g0, row0 + count), every gstep-th, at positions from pos0
+    auto rows = [&](uint32_t row0, uint32_t pos0, uint32_t count, uint32_t g0, uint32_t gstep) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(xyz) & 15) == 0) && (row0 & 3u) == 0;
+        const bool vst = (pos0 & 3u) == 0;
+        for (uint32_t gi = g0; 4 * gi < count; gi += gstep) {
+            const uint32_t cnt = min(4u, count - 4 * gi);
+            float f[12];
+            load_rows4(xyz, row0 + 4 * gi, cnt, vec, f);
+            KeyT k[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int32_t q[3];
+            for (int u = 0; u < 4; ++u) {
+                int32_t q[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) quantize1(f[3 * u + a], q[a]);
-            uint32_t c[3], off[3];
-            g.cell_of(q, c, off);
-            k[u] = g.key_of<KeyT>(c, off);
-            v[u] = g.payload_of(off, i0 + u);
-        }
-        if (!STORE) {
-        } else if (cnt == 4) {
-            if (sizeof(KeyT) == 4) {
-                reinterpret_cast<uint4 *>(keys)[gi] =
-                    make_uint4((uint32_t)k[0], (uint32_t)k[1], (uint32_t)k[2], (uint32_t)k[3]);
-            } else {
-                reinterpret_cast<ulonglong2 *>(keys)[2 * gi] = make_ulonglong2(k[0], k[1]);
-                reinterpret_cast<ulonglong2 *>(keys)[2 * gi + 1] = make_ulonglong2(k[2], k[3]);
+                for (int a = 0; a < 3; ++a) quantize1(f[3 * u + a], q[a]);
+                uint32_t c[3], off[3];
+                g.cell_of(q, c, off);
+                k[u] = g.key_of<KeyT>(c, off);
             }
-            if (PACKED) {
-                reinterpret_cast<ulonglong2 *>(vals)[2 * gi] = make_ulonglong2(v[0], v[1]);
-                reinterpret_cast<ulonglong2 *>(vals)[2 * gi + 1] = make_ulonglong2(v[2], v[3]);
+            if (STORE) {
+                const uint32_t p = pos0 + 4 * gi;
+                if (cnt == 4 && vst) {
+                    if (sizeof(KeyT) == 4) {
+                        reinterpret_cast<uint4 *>(keys + p)[0] =
+                            make_uint4((uint32_t)k[0], (uint32_t)k[1], (uint32_t)k[2], (uint32_t)k[3]);
+                    } else {
+                        reinterpret_cast<ulonglong2 *>(keys + p)[0] = make_ulonglong2(k[0], k[1]);
+                        reinterpret_cast<ulonglong2 *>(keys + p)[1] = make_ulonglong2(k[2], k[3]);
+                    }
+                } else {
+                    for (uint32_t u = 0; u < cnt; ++u) keys[p + u] = k[u];
+                }
             }
-        } else {
-            for (uint32_t u = 0; u < cnt; ++u) {
-                keys[i0 + u] = k[u];
-                if (PACKED) vals[i0 + u] = v[u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if ((uint32_t)u >= cnt) break;
+                for (int p = 0; p < np; ++p)
+                    atomicAdd(&h[p][(uint32_t)(k[u] >> (p * kRadixBits)) & 255u], 1u);
             }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if ((uint32_t)u >= cnt) break;
-            for (int p = 0; p < np; ++p)
-                atomicAdd(&h[p][(uint32_t)(k[u] >> (p * kRadixBits)) & 255u], 1u);
+    };
+    if (!MULTI) {  // one frame: the whole grid sweeps its rows
+        cur = 0;
+        rows(fr[0].in_off, 0u, ctl->n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    } else {
+        const UnitRange ur = block_units(prm.ntiles, prm.nf);
+        for (uint32_t u = ur.lo; u < ur.hi; u += ur.step) {
+            const TileSpan sp = unit_span(fr, prm.nf, u);
+            if (sp.f != cur) {
+                if (cur != 0xffffffffu) flush();
+                cur = sp.f;
+                g.set_frame(fr[sp.f]);
+            }
+            rows(fr[sp.f].in_off + sp.first, fr[sp.f].pos_off + sp.first, sp.count, threadIdx.x,
+                 blockDim.x);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {
-        const uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(&ctl->hist[i / kRadixBins][i % kRadixBins], v);
-    }
+    if (cur != 0xffffffffu) flush();
 }
 
 // The key kernel for either key width (the plan selects it on the device).
-template <bool PACKED, bool STORE>
+template <bool STORE, bool MULTI>
 __global__ void __launch_bounds__(256)
-    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, void *__restrict__ keys,
-           unsigned long long *__restrict__ vals, Clears clr)
+    k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, const Frame *__restrict__ fr,
+           uint32_t *__restrict__ fhist, void *__restrict__ keys, Clears clr)
 {
     __shared__ uint32_t h[kMaxPasses][kRadixBins];
     if (plan->sort.key64)
-        keys_body<unsigned long long, PACKED, STORE>(xyz, plan, prm, (unsigned long long *)keys, vals,
-                                                     clr, h);
+        keys_body<unsigned long long, STORE, MULTI>(xyz, plan, prm, fr, fhist, (unsigned long long *)keys,
+                                                    clr, h);
     else
-        keys_body<uint32_t, PACKED, STORE>(xyz, plan, prm, (uint32_t *)keys, vals, clr, h);
+        keys_body<uint32_t, STORE, MULTI>(xyz, plan, prm, fr, fhist, (uint32_t *)keys, clr, h);
 }
 
 // a3: cell table from the sorted keys, in one pass with a decoupled look-back
@@ -325,6 +472,9 @@ __global__ void __launch_bounds__(256)
 //   sc_start[a]   first sorted position of sub-cell a (sc_start[M_s] = n)
 //   scode[a]      sub-cell code of a: which half of its cell on each axis
 //   cell_key[c]   cell key of cell c; cell_sc[c] first sub-cell of cell c
+//   cframe[c]     frame of cell c
+// A frame's first position always starts a new cell and sub-cell (keys are
+// frame-local, so two frames' cells never merge).
 struct CellsSmem {
     uint32_t tile;
     unsigned long long warp[kScanThreads / 32];
@@ -333,7 +483,7 @@ struct CellsSmem {
     uint32_t sc[kScanTile];
 };
 
-template <typename KeyT, typename ValT>
+template <typename KeyT, typename ValT, bool MULTI>
 __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const KeyT *__restrict__ keys_a,
                                            const ValT *__restrict__ vals_a,
                                            const KeyT *__restrict__ keys_b,
@@ -343,6 +493,8 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
                                            uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
                                            unsigned long long *__restrict__ cell_key,
                                            uint32_t *__restrict__ cell_sc,
+                                           uint32_t *__restrict__ cframe,
+                                           const Frame *__restrict__ fr,
                                            unsigned long long *__restrict__ tstat, CellsSmem &C)
 {
     const SortCtl *ctl = &plan->sort;
@@ -354,8 +506,10 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
     const ValT *__restrict__ vals = in_b ? vals_b : vals_a;
     constexpr bool PACKED = sizeof(ValT) == 8;
     GridMap g;
-    if (PACKED) g.load(plan, prm);
+    if (PACKED) g.load(plan, prm, fr[0]);
+    uint32_t gframe = 0;  // frame whose origin g holds
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    const uint32_t nf = prm.nf;
 
     constexpr unsigned long long kAgg = 1ull << 62, kIncl = 2ull << 62;
     constexpr unsigned long long kMask = (1ull << 62) - 1;
@@ -376,6 +530,24 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
         KeyT k[kScanIPT];
         unsigned long long flag[kScanIPT];  // (cell head << 31) | sub-cell head
         KeyT prev = (p0 > 0 && p0 - 1 < n) ? keys[p0 - 1] : KeyT(0);
+        // frame of the thread's first position, and which of its positions
+        // start a frame (bit i: position p0 + i)
+        const uint32_t f0 = (MULTI && p0 < n) ? frame_of_pos(fr, nf, p0) : 0u;
+        uint32_t fstarts = p0 == 0 ? 1u : 0u;
+        if (MULTI) {
+            uint32_t wf = f0, wstart = fr[f0].pos_off;
+            uint32_t wnext = wf + 1 < nf ? fr[wf + 1].pos_off : 0xffffffffu;
+#pragma unroll
+            for (int i = 0; i < kScanIPT; ++i) {
+                const uint32_t p = p0 + i;
+                while (p >= wnext) {
+                    ++wf;
+                    wstart = wnext;
+                    wnext = wf + 1 < nf ? fr[wf + 1].pos_off : 0xffffffffu;
+                }
+                if (p == wstart) fstarts |= 1u << i;
+            }
+        }
         unsigned long long run = 0;
         const bool full = p0 + kScanIPT <= n;
         if (full) {  // the thread's keys in 16-byte loads
@@ -409,8 +581,9 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             unsigned long long f = 0;
             if (p < n) {
                 if (!full) k[i] = keys[p];
-                const bool sh = (p == 0) || k[i] != prev;
-                const bool ch = (p == 0) || (k[i] >> 3) != (prev >> 3);
+                const bool fh = (fstarts >> i) & 1u;  // includes p == 0
+                const bool sh = fh || k[i] != prev;
+                const bool ch = fh || (k[i] >> 3) != (prev >> 3);
                 f = ((unsigned long long)ch << 31) | (unsigned long long)sh;
                 prev = k[i];
             } else {
@@ -481,10 +654,16 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
 
         unsigned long long before = base;
+        uint32_t fcur = f0;
 #pragma unroll
         for (int i = 0; i < kScanIPT; ++i) {
             const uint32_t p = p0 + i;
             if (p >= n) break;
+            if (i > 0 && ((fstarts >> i) & 1u)) ++fcur;
+            if (MULTI && PACKED && fcur != gframe) {  // the grid origin of the position's frame
+                g.set_frame(fr[fcur]);
+                gframe = fcur;
+            }
             const unsigned long long cur = base + flag[i];
             const uint32_t sc = (uint32_t)(cur & 0x7fffffffull) - 1u;
             const uint32_t c = (uint32_t)(cur >> 31) - 1u;
@@ -492,7 +671,7 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             const bool ch = (cur >> 31) != (before >> 31);
             before = cur;
             const uint32_t idx = (uint32_t)vv[i];
-            if (sc >= n || c >= n || idx >= n) {  // only after a look-back timeout
+            if (sc >= n || c >= n || idx >= prm.rows) {  // only after a look-back timeout
                 atomicOr(&plan->status, ST_SIZE_OVERFLOW);
                 continue;
             }
@@ -504,6 +683,7 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             if (ch) {
                 cell_key[c] = (unsigned long long)(k[i] >> 3);
                 cell_sc[c] = sc;
+                if (MULTI) cframe[c] = fcur;
             }
             Rec r;
             if (PACKED) {
@@ -540,24 +720,25 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
 
 // The cell-table kernel for either key width (the plan selects it on the
 // device); the payload width is known on the host.
-template <typename ValT>
-__global__ void __launch_bounds__(kScanThreads, 4)
+template <typename ValT, bool MULTI>
+__global__ void __launch_bounds__(kScanThreads, MULTI ? 3 : 4)  // the frame walk needs registers
     k_cells(Plan *plan, Params prm, const void *__restrict__ keys_a, const ValT *__restrict__ vals_a,
             const void *__restrict__ keys_b, const ValT *__restrict__ vals_b,
             const float *__restrict__ xyz, Rec *__restrict__ rec, uint32_t *__restrict__ sc_of,
             uint32_t *__restrict__ sc_start, uint8_t *__restrict__ scode,
             unsigned long long *__restrict__ cell_key, uint32_t *__restrict__ cell_sc,
+            uint32_t *__restrict__ cframe, const Frame *__restrict__ fr,
             unsigned long long *__restrict__ tstat)
 {
     __shared__ CellsSmem C;
     using u64 = unsigned long long;
     if (plan->sort.key64)
-        cells_body<u64, ValT>(plan, prm, (const u64 *)keys_a, vals_a, (const u64 *)keys_b, vals_b, xyz,
-                              rec, sc_of, sc_start, scode, cell_key, cell_sc, tstat, C);
+        cells_body<u64, ValT, MULTI>(plan, prm, (const u64 *)keys_a, vals_a, (const u64 *)keys_b, vals_b, xyz,
+                              rec, sc_of, sc_start, scode, cell_key, cell_sc, cframe, fr, tstat, C);
     else
-        cells_body<uint32_t, ValT>(plan, prm, (const uint32_t *)keys_a, vals_a,
+        cells_body<uint32_t, ValT, MULTI>(plan, prm, (const uint32_t *)keys_a, vals_a,
                                    (const uint32_t *)keys_b, vals_b, xyz, rec, sc_of, sc_start,
-                                   scode, cell_key, cell_sc, tstat, C);
+                                   scode, cell_key, cell_sc, cframe, fr, tstat, C);
 }
 
 // The nominal (grid) centre of the sub-cell containing q, as the cell origin
@@ -578,6 +759,16 @@ __device__ __forceinline__ void subcell_centre(const int32_t q[3], const int32_t
     }
 }
 
+// Grid origin (bounding-box corner) of the frame holding sorted position p.
+__device__ __forceinline__ void frame_origin(const Frame *__restrict__ fr, uint32_t nf, uint32_t p,
+                                             int32_t lo[3])
+{
+    const Frame &F = fr[frame_of_pos(fr, nf, p)];
+    lo[0] = F.lo[0];
+    lo[1] = F.lo[1];
+    lo[2] = F.lo[2];
+}
+
 __device__ __forceinline__ float centre_dist2(const Rec &r, const int32_t org[3],
                                               const int32_t cen2[3])
 {
@@ -596,11 +787,12 @@ __global__ void __launch_bounds__(256)
                     const uint32_t *__restrict__ sc_start, SubBox *__restrict__ box,
                     uint32_t *__restrict__ sminidx, uint32_t *__restrict__ parent,
                     uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
-                    int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps)
+                    int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps,
+                    const Frame *__restrict__ fr)
 {
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
-    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
+    const int32_t lo0[3] = {fr[0].lo[0], fr[0].lo[1], fr[0].lo[2]};  // one frame: its origin
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x) {
         parent[a] = a;
         csize[a] = 0;
@@ -614,7 +806,7 @@ __global__ void __launch_bounds__(256)
             reps[a] = kNoRep;
             continue;
         }
-        if (e - s > (uint32_t)kBigSubcell) {
+        if (e - s > prm.big_subcell) {
             // medium sub-cells from the front of the list, huge ones from its middle
             // (at most n/65 and n/2049 of them)
             if (e - s > (uint32_t)kHugeSubcell) big[plan->sort.n / 2 + atomicAdd(&plan->n_huge, 1u)] = a;
@@ -628,6 +820,8 @@ __global__ void __launch_bounds__(256)
         const Rec r0 = rec[s];
         int32_t org[3], cen2[3];
         const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        int32_t lo[3] = {lo0[0], lo0[1], lo0[2]};
+        if (prm.nf > 1) frame_origin(fr, prm.nf, s, lo);
         subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
         float best = __int_as_float(0x7f800000);
         Rec rp = r0;
@@ -656,11 +850,11 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_subcell_big(Plan *plan, Params prm, const Rec *__restrict__ rec,
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps)
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
+                  const Frame *__restrict__ fr)
 {
     if (call_aborted(&plan->status)) return;
     const uint32_t nb = plan->n_big;
-    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     const int l = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < nb; j += nwarps) {
@@ -669,6 +863,8 @@ __global__ void __launch_bounds__(256)
         const Rec r0 = rec[s];
         int32_t org[3], cen2[3];
         const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        int32_t lo[3];
+        frame_origin(fr, prm.nf, s, lo);
         subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
         int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
         uint32_t mi = 0xffffffffu;
@@ -712,14 +908,14 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_subcell_huge(Plan *plan, Params prm, const Rec *__restrict__ rec,
                   const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps)
+                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
+                  const Frame *__restrict__ fr)
 {
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
     if (block_aborted(&plan->status)) return;
     const uint32_t nb = plan->n_huge;
     big += plan->sort.n / 2;
-    const int32_t lo[3] = {plan->lo[0], plan->lo[1], plan->lo[2]};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
         const uint32_t a = big[j];
@@ -727,6 +923,8 @@ __global__ void __launch_bounds__(256)
         const Rec r0 = rec[s];
         int32_t org[3], cen2[3];
         const int32_t q0[3] = {r0.x, r0.y, r0.z};
+        int32_t lo[3];
+        frame_origin(fr, prm.nf, s, lo);
         subcell_centre(q0, lo, prm.S, prm.h, org, cen2);
         int32_t L[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, H[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
         uint32_t mi = 0xffffffffu;
@@ -806,7 +1004,8 @@ __global__ void __launch_bounds__(256)
             const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
             uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
             uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
-            uint8_t *__restrict__ cocc)
+            uint8_t *__restrict__ cocc, const uint32_t *__restrict__ cframe,
+            const Frame *__restrict__ fr, uint32_t nf)
 {
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
@@ -818,8 +1017,13 @@ __global__ void __launch_bounds__(256)
         const unsigned long long x = k >> sh, col = k >> b2;
         const unsigned long long kp = c > 0 ? cell_key[c - 1] : ~0ull;
         const unsigned long long kn = c + 1 < M ? cell_key[c + 1] : ~0ull;
-        if (c == 0 || (kp >> sh) != x) slab_lo[x] = c;
-        if (c + 1 == M || (kn >> sh) != x) slab_hi[x] = c + 1;
+        // slab x of the cell's frame; a frame change also ends a slab
+        const uint32_t f = nf > 1 ? cframe[c] : 0u;
+        const bool fprev = nf > 1 && c > 0 && cframe[c - 1] != f;
+        const bool fnext = nf > 1 && c + 1 < M && cframe[c + 1] != f;
+        const uint32_t se = fr[f].slab_base + (uint32_t)x;
+        if (c == 0 || fprev || (kp >> sh) != x) slab_lo[se] = c;
+        if (c + 1 == M || fnext || (kn >> sh) != x) slab_hi[se] = c + 1;
         if (cols) {
             if (c == 0 || (kp >> b2) != col) col_lo[col] = c;
             if (c + 1 == M || (kn >> b2) != col) col_hi[col] = c + 1;
@@ -833,19 +1037,29 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st)
+cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, const FrontArgs &fa,
+                          cudaStream_t st)
 {
-    const int grid = grid_for(ws, prm.n, 1024, 8);  // four points per thread
-    k_init<<<1, 256, 0, st>>>(ws.plan, prm.n, (uint32_t)kept_sort_passes(prm.n), prm.wait_cap);
+    // one frame: four points per thread over the whole grid; several:
+    // blocks take contiguous runs of 1024-point units (frame-aligned)
+    const bool multi = prm.nf > 1;
+    const int grid = multi ? (int)std::min<uint64_t>((uint64_t)prm.ntiles * kUnitsPerTile,
+                                                     (uint64_t)ws.sms * 8)
+                           : grid_for(ws, prm.n, 1024, 8);
+    const uint64_t hist_words = (uint64_t)prm.nf * kMaxPasses * kRadixBins;
+    const int igrid = (int)std::min<uint64_t>((hist_words + 2047) / 2048, (uint64_t)ws.sms * 4);
+    k_init<<<igrid < 1 ? 1 : igrid, 256, 0, st>>>(ws.plan, ws.frames, prm.nf, ws.fhist, prm.n,
+                                                  (uint32_t)kept_sort_passes(prm.rows), prm.wait_cap,
+                                                  fa.single ? 1 : 0, fa.min_size, fa.max_size);
     FEC_MARK(ws, "k_init", st);
-    k_bbox<<<grid, 256, 0, st>>>(xyz, prm.n, ws.plan);
+    if (multi) k_bbox<true><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
+    else k_bbox<false><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
     FEC_MARK(ws, "k_bbox", st);
-    k_plan<<<1, 32, 0, st>>>(ws.plan, prm);
+    k_plan<<<1, 256, 0, st>>>(ws.plan, ws.frames, prm);
     FEC_MARK(ws, "k_plan", st);
-    auto *va = (unsigned long long *)ws.vals_a;
     Clears clr;
     clr.sort_status = ws.sort_status;
-    clr.sort_words = sort_status_words(prm.n) / 2;
+    clr.sort_words = ((size_t)prm.ntiles + 1) * kRadixBins;  // look-back array 0, this call's tiles
     clr.scan_status = ws.scan_status;
     clr.scan_words = (size_t)prm.n / kScanTile + 2;
     clr.slab_lo = ws.slab_lo;
@@ -854,10 +1068,14 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cu
     clr.max_words = clr.sort_words > clr.scan_words ? clr.sort_words : clr.scan_words;
     if (clr.slab_words > clr.max_words) clr.max_words = clr.slab_words;
     // packed layout: the sort's first pass computes the keys itself
-    if (prm.packed)
-        k_keys<true, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+    if (prm.packed && !multi)
+        k_keys<false, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+    else if (prm.packed)
+        k_keys<false, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+    else if (!multi)
+        k_keys<true, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     else
-        k_keys<false, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.keys_a, va, clr);
+        k_keys<true, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     FEC_MARK(ws, "k_keys", st);
     return cudaGetLastError();
 }
@@ -869,28 +1087,38 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item per thread
     using u32 = uint32_t;
     using u64 = unsigned long long;
-    if (prm.packed)
-        k_cells<u64><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, ws.keys_a, (const u64 *)ws.vals_a, ws.keys_b, (const u64 *)ws.vals_b, xyz,
-            ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc, ws.scan_status);
+    // one frame, or several (frame starts, frame origins, cell frames)
+    const u64 *va64 = (const u64 *)ws.vals_a, *vb64 = (const u64 *)ws.vals_b;
+    const u32 *va32 = (const u32 *)ws.vals_a, *vb32 = (const u32 *)ws.vals_b;
+#define FEC_CELLS_ARGS(va, vb)                                                                   \
+    ws.plan, prm, ws.keys_a, va, ws.keys_b, vb, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode,     \
+        ws.cell_key, ws.cell_sc, ws.cframe, ws.frames, ws.scan_status
+    if (prm.packed && prm.nf == 1)
+        k_cells<u64, false><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va64, vb64));
+    else if (prm.packed)
+        k_cells<u64, true><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va64, vb64));
+    else if (prm.nf == 1)
+        k_cells<u32, false><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va32, vb32));
     else
-        k_cells<u32><<<grid, kScanThreads, 0, st>>>(
-            ws.plan, prm, ws.keys_a, (const u32 *)ws.vals_a, ws.keys_b, (const u32 *)ws.vals_b, xyz,
-            ws.rec, ws.sc_of, ws.sc_start, ws.scode, ws.cell_key, ws.cell_sc, ws.scan_status);
+        k_cells<u32, true><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va32, vb32));
+#undef FEC_CELLS_ARGS
     FEC_MARK(ws, "k_cells", st);
     k_subcell_stats<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
-                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps);
+                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps,
+                                           ws.frames);
     FEC_MARK(ws, "k_subcell_stats", st);
-    k_subcell_big<<<grid_for(ws, prm.n / (kBigSubcell + 1), 8, 4), 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
-                                              ws.sminidx, ws.reps);
+    k_subcell_big<<<grid_for(ws, prm.n / (prm.big_subcell + 1), 8, 4), 256, 0, st>>>(
+        ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box, ws.sminidx, ws.reps, ws.frames);
     FEC_MARK(ws, "k_subcell_big", st);
-    k_subcell_huge<<<grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2), 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box,
-                                               ws.sminidx, ws.reps);
+    k_subcell_huge<<<grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2), 256, 0, st>>>(
+        ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box, ws.sminidx, ws.reps, ws.frames);
     FEC_MARK(ws, "k_subcell_huge", st);
-    k_clear_cols<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
-    FEC_MARK(ws, "k_clear_cols", st);
+    if (prm.nf == 1) {  // the dense column index serves single clouds only
+        k_clear_cols<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
+        FEC_MARK(ws, "k_clear_cols", st);
+    }
     k_slabs<<<grid1, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
-                                  ws.col_lo, ws.col_hi, ws.cocc);
+                                  ws.col_lo, ws.col_hi, ws.cocc, ws.cframe, ws.frames, prm.nf);
     FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile
 constexpr int kBigSubcell = 64;          // sub-cells above this size are reduced by a warp,
 constexpr int kHugeSubcell = 2048;       //   above this size by a block
+constexpr uint32_t kMaxFramesPerCall = 4096;  // frames of one call (one radius group)
 constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept per block
 #ifndef FEC_REGION_CELLS
 #define FEC_REGION_CELLS 1024
@@ -100,13 +101,63 @@ struct SortCtl {
     uint32_t key64;     // 1: 64-bit keys, 0: 32-bit keys
     uint32_t parity;    // pass p uses look-back array (p + parity) & 1, which starts clear
     uint32_t wait_cap;  // spin iterations of a look-back wait before it gives up
-    uint32_t hist[kMaxPasses][kRadixBins];   // digit counts of every pass
+    uint32_t hist[kMaxPasses][kRadixBins];   // digit counts of every pass (unsegmented sorts)
     uint32_t tile_counter[kMaxPasses];       // dynamic tile ids of every pass
 };
 
+// One frame of a call.  A call clusters nf independent clouds ("frames")
+// that share the radius d in one pass of the pipeline: frame f's points are
+// rows in_off .. in_off+n-1 of the call's input (and of its labels) and
+// positions pos_off .. pos_off+n-1 of the sorted arrays; keys are
+// frame-local, the sort is segmented by frame (its tiles never straddle
+// two frames), cells and sub-cells of different frames never meet, and the
+// kept components of each frame are numbered from 0.  A single cloud is the
+// frame table {0, 0, n}.  Static fields are written by the host (or by
+// k_init for a single cloud); the rest on the device.
+struct __align__(16) Frame {
+    uint32_t in_off;     // first input row
+    uint32_t pos_off;    // first sorted position
+    uint32_t n;          // points (> 0)
+    uint32_t tile0;      // first tile of the frame in the sort (kSortTile points each)
+    long long min_size, max_size;  // inclusive size bounds of kept clusters
+    int32_t lo[3];       // bounding box of q per original axis (device)
+    uint32_t kept;       // kept clusters (device)
+    int32_t hi[3];
+    uint32_t nslab;      // slab-index entries: the frame's largest major cell coordinate + 1 (device)
+    uint32_t slab_base;  // first slab-index entry of the frame (device)
+    uint32_t pad[3];
+};
+
+// Frame of a sorted position, of an input row, of a sort tile: the last
+// frame whose first one is at or before it (frames are in input order and
+// none is empty, so these offsets increase strictly).
+__device__ __forceinline__ uint32_t frame_search(const Frame *__restrict__ fr, uint32_t nf,
+                                                 uint32_t v, int field)
+{
+    uint32_t lo = 0, hi = nf;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t at = field == 0 ? fr[mid].pos_off : (field == 1 ? fr[mid].in_off : fr[mid].tile0);
+        if (at <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ uint32_t frame_of_pos(const Frame *fr, uint32_t nf, uint32_t p)
+{
+    return nf > 1 ? frame_search(fr, nf, p, 0) : 0u;
+}
+__device__ __forceinline__ uint32_t frame_of_row(const Frame *fr, uint32_t nf, uint32_t i)
+{
+    return nf > 1 ? frame_search(fr, nf, i, 1) : 0u;
+}
+__device__ __forceinline__ uint32_t frame_of_tile(const Frame *fr, uint32_t nf, uint32_t t)
+{
+    return nf > 1 ? frame_search(fr, nf, t, 2) : 0u;
+}
+
 // Per-call plan (device memory), written by k_plan / k_cells / kernels.
 struct Plan {
-    int32_t lo[3], hi[3];      // bounding box of q per original axis
     int32_t perm[3];           // permuted axis p -> original axis (p0 major .. p2 minor)
     uint32_t bits[3];          // bits of the cell coordinate per permuted axis
     uint32_t key_bits;         // total sort-key bits (cell key bits + 3)
@@ -119,6 +170,7 @@ struct Plan {
     uint32_t use_cols;          // 1: the dense column index covers the grid
     uint32_t edges_n;           // boundary edges emitted by the neighbour step
     uint32_t region_counter;    // dynamic regions of the neighbour step
+    uint32_t slab_need;         // slab-index entries the frames need (all frames)
     unsigned long long ctr[8];  // work counters of the union step (CTR_*)
     SortCtl sort;              // main (key, index) sort
     SortCtl kept;              // sort of kept components by smallest index
@@ -138,6 +190,15 @@ struct Params {
     uint32_t div_m, div_s;
     uint32_t wait_cap = kWaitCap;    // iterations of a look-back wait before it gives up
     uint32_t union_cap = kUnionCap;  // steps of a union or find before it gives up
+    // frames of the call (see Frame): nf, their sort tiles, and the length
+    // of the call's input / label arrays (rows)
+    uint32_t nf = 1;
+    uint32_t ntiles = 0;
+    uint32_t rows = 0;
+    // tunables: largest region of the neighbour step (cells, 64..1024) and
+    // the sub-cell size above which a warp, not a thread, reduces a sub-cell
+    uint32_t region_cells = kRegionCellsPerBlock;
+    uint32_t big_subcell = kBigSubcell;
 };
 
 // Quantised point record in cell order: coordinates and the original index.
@@ -187,12 +248,12 @@ struct GridMap {
     int32_t S, h;
     uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
 
-    __device__ __forceinline__ void load(const Plan *plan, const Params &prm)
+    __device__ __forceinline__ void load(const Plan *plan, const Params &prm, const Frame &fr)
     {
         const uint32_t b0 = plan->bits[0], b1 = plan->bits[1], b2 = plan->bits[2];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {  // constant indices only (no local memory)
-            lo[a] = plan->lo[a];
+            lo[a] = fr.lo[a];
             const int p = plan->perm[0] == a ? 0 : (plan->perm[1] == a ? 1 : 2);
             ksh[a] = 3u + (p == 0 ? b1 + b2 : (p == 1 ? b2 : 0u));
             kbit[a] = 2u - (uint32_t)p;
@@ -202,6 +263,12 @@ struct GridMap {
         h = prm.h;
         div_m = prm.div_m;
         div_s = prm.div_s;
+    }
+    // Another frame of the same call: only the grid origin changes.
+    __device__ __forceinline__ void set_frame(const Frame &fr)
+    {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lo[a] = fr.lo[a];
     }
     // Cell coordinate and offset inside the cell, per original axis.
     __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
@@ -366,6 +433,9 @@ struct Workspace {
     int sms = 0;
     size_t cap_n = 0;
     uint32_t slab_cap = 0;
+    uint32_t nf_cap = 1;           // frames the table holds
+    Frame *frames = nullptr;       // frame table (nf_cap)
+    uint32_t *fhist = nullptr;     // per frame: digit counts of every pass of the main sort
     void *base = nullptr;
     size_t bytes = 0;
     Plan *plan = nullptr;
@@ -391,6 +461,7 @@ struct Workspace {
     uint32_t *big = nullptr;
     unsigned long long *cell_key = nullptr;
     uint32_t *cell_sc = nullptr;   // cap_n + 1
+    uint32_t *cframe = nullptr;    // per cell: its frame
     uint32_t *slab_lo = nullptr;   // slab_cap
     uint32_t *slab_hi = nullptr;
     uint2 *pairq = nullptr;        // sub-cell pairs queued for point tests
@@ -454,9 +525,16 @@ inline uint32_t region_scratch(const Workspace &ws, uint64_t n)
     return (uint32_t)(kRegionScratch * rc / kRegionCellsPerBlock);
 }
 
-// Bytes of a workspace for cap_n points and slab_cap slab entries; with a
-// non-null base, also carves the arrays into ws.
-size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap);
+// Bytes of a workspace for cap_n points, slab_cap slab entries and nf_cap
+// frames; with a non-null base, also carves the arrays into ws.
+size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_cap,
+                        uint32_t nf_cap = 1);
+// Sort tiles of a frame of n points, and the tiles a workspace must hold.
+inline uint32_t frame_tiles(uint64_t n) { return (uint32_t)((n + kSortTile - 1) / kSortTile); }
+inline uint32_t max_tiles(size_t cap_n, uint32_t nf_cap)
+{
+    return (uint32_t)(cap_n / kSortTile) + nf_cap + 1;
+}
 
 // Host-side constants for n points at radius d.
 Params make_params(uint32_t n, float d);
@@ -465,21 +543,32 @@ int max_sort_passes(const Params &prm);
 // Passes of the kept-component sort (keys are point indices < n).
 int kept_sort_passes(uint32_t n);
 
-// a1 (init, bbox, plan, keys) for n points at xyz (device).
-cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st);
+// How a call's frame table is set: by k_init for a single cloud (single =
+// true, with its size bounds), else uploaded by the host before the call.
+struct FrontArgs {
+    bool single = true;
+    long long min_size = 0, max_size = 0;
+};
+// a1 (init, bbox, plan, keys) for the call's prm.n points at xyz (device).
+cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, const FrontArgs &fa,
+                          cudaStream_t st);
 // a3 (cell table, sub-cell stats, slab index).
 cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st);
-// a4 + a5 + kept list of a6.
-cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
-                          long long max_size, cudaStream_t st);
-// a6 rank + labels (labels: device pointer, n entries).
-cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool packed,
+// a4 + a5 + kept list of a6 (size bounds from the frame table).
+cudaError_t enqueue_union(Workspace &ws, const Params &prm, cudaStream_t st);
+// a6 rank + labels (labels: device pointer, prm.rows entries; fill: set
+// every label to -1 first, else the caller has done so).
+cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool fill,
                            cudaStream_t st);
-// The whole pipeline for one cloud of prm.n points (device pointers), no host
-// synchronisation.  prm comes from make_params(n, d); callers may lower its
-// slab capacity or iteration caps.
+// The whole pipeline for one call (device pointers), no host
+// synchronisation: prm.nf frames of prm.n points in total that share the
+// radius, rows prm.rows of xyz and labels.  prm comes from make_params(n, d)
+// (one frame); callers may lower its slab capacity or iteration caps, or lay
+// out several frames (the table then uploaded before the call, fa.single
+// false).  fill_labels: set all prm.rows labels to -1 first (else the caller
+// has done so).
 cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm,
-                            long long min_size, long long max_size, int32_t *labels,
+                            const FrontArgs &fa, int32_t *labels, bool fill_labels,
                             cudaStream_t st);
 
 // Onesweep radix sort of (key, value) over ctl->npasses 8-bit digits, with
@@ -491,32 +580,44 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm,
 // Where the first pass of a sort gets its keys: from keys_a/vals_a (xyz
 // null), or computed from the coordinates under the plan (packed payloads;
 // the key kernel then only makes the histograms).
+// The frames (non-null: a segmented sort, see k_onesweep) and their digit
+// histograms.
 struct SortSource {
     const float *xyz = nullptr;
     const Plan *plan = nullptr;
     Params prm{};
+    const Frame *frames = nullptr;
+    const uint32_t *fhist = nullptr;
 };
+// tiles: how many tiles the sort can have at most (sizes the grid).
 cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, void *keys_a,
                         void *vals_a, void *keys_b, void *vals_b, bool key64, bool val64,
-                        bool identity_vals, uint32_t *tile_status, uint32_t max_n, int max_passes,
+                        bool identity_vals, uint32_t *tile_status, uint32_t tiles, int max_passes,
                         int grid, cudaStream_t st, uint32_t *status,
                         const SortSource &src = SortSource());
 // The main sort's source, matching enqueue_front (which stores keys only
-// when the payloads are not packed).
+// when the payloads are not packed): segmented by the call's frames.
 inline SortSource main_sort_source(const Workspace &ws, const float *xyz, const Params &prm)
 {
     SortSource s;
+    s.prm = prm;
+    s.frames = ws.frames;
+    s.fhist = ws.fhist;
     if (prm.packed) {
         s.xyz = xyz;
         s.plan = ws.plan;
-        s.prm = prm;
     }
     return s;
 }
-// uint32 words of look-back status a sort of up to max_n keys needs.
-inline size_t sort_status_words(uint32_t max_n)
+// uint32 words between the two look-back arrays of a workspace's sorts.
+inline size_t sort_tstride(const Workspace &ws)
 {
-    return 2 * (((size_t)max_n + kSortTile - 1) / kSortTile + 1) * kRadixBins;
+    return ((size_t)max_tiles(ws.cap_n, ws.nf_cap) + 1) * kRadixBins;
+}
+// uint32 words of look-back status (two arrays) for a sort of `tiles` tiles.
+inline size_t sort_status_words(uint32_t tiles)
+{
+    return 2 * ((size_t)tiles + 1) * kRadixBins;
 }
 // Digit histograms of all passes for 32-bit keys already in memory.
 cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, const uint32_t *status, int grid,

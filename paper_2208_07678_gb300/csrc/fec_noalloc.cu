@@ -121,7 +121,11 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
     int32_t *lout = dev_out ? labels : ws.labels;
 
     // The same stages as fec_cluster, on the static workspace.
-    cudaError_t e = enqueue_cluster(ws, xin, prm, min_size, max_size, lout, st);
+    FrontArgs fa;
+    fa.single = true;
+    fa.min_size = min_size;
+    fa.max_size = max_size;
+    cudaError_t e = enqueue_cluster(ws, xin, prm, fa, lout, true, st);
     if (e == cudaSuccess && !dev_out)
         e = cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
     uint32_t status_bits = 0, k = 0;

@@ -198,7 +198,7 @@ __device__ __forceinline__ int box_decide(const SubBox &A, const SubBox &B, uint
 __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long long n1,
                                             unsigned long long z_lo, unsigned long long z_hi,
                                             uint32_t b1, uint32_t b2, const Plan *plan,
-                                            uint32_t slab_cap,
+                                            uint32_t slab_base, uint32_t nslab,
                                             const unsigned long long *__restrict__ cell_key,
                                             const uint32_t *__restrict__ slab_lo,
                                             const uint32_t *__restrict__ slab_hi,
@@ -211,9 +211,9 @@ __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long
         lo = col_lo[col];
         end = col_hi[col];
     } else {
-        if (n0 >= slab_cap) return 0;
-        lo = slab_lo[n0];
-        end = slab_hi[n0];
+        if (n0 >= nslab) return 0;  // beyond the frame's slabs
+        lo = slab_lo[slab_base + n0];
+        end = slab_hi[slab_base + n0];
     }
     const unsigned long long colkey = (n0 << (b1 + b2)) | (n1 << b2);
     const unsigned long long tlo = colkey | z_lo, thi = colkey | z_hi;
@@ -234,11 +234,11 @@ __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long
 // The half-stencil neighbour cells of cell c (13 of the 26; the other half
 // is covered by the neighbours' own visits), one column per lane: lanes
 // 0..3 take columns (0,+1), (+1,-1), (+1,0), (+1,+1) over dz in {-1,0,+1},
-// lane 4 takes (0,0,+1), the next cell of the same column.  Each lane
-// returns its cells in f[0..2] and their count.
+// lane 4 takes (0,0,+1), the next cell of the same column (of the same
+// frame).  Each lane returns its cells in f[0..2] and their count.
 __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, unsigned long long ck,
                                             uint32_t b1, uint32_t b2, const Plan *plan,
-                                            uint32_t slab_cap,
+                                            uint32_t slab_base, uint32_t nslab, bool next_same,
                                             const unsigned long long *__restrict__ cell_key,
                                             const uint32_t *__restrict__ slab_lo,
                                             const uint32_t *__restrict__ slab_hi,
@@ -248,7 +248,7 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
     const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
     const unsigned long long c0 = ck >> (b1 + b2), c1 = (ck >> b2) & m1, c2 = ck & m2;
     if (lane == 4) {
-        if (c2 < m2 && c + 1 < M && cell_key[c + 1] == ck + 1) {
+        if (c2 < m2 && c + 1 < M && next_same && cell_key[c + 1] == ck + 1) {
             f[0] = c + 1;
             return 1;
         }
@@ -261,8 +261,8 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
     const unsigned long long m0 = (1ull << plan->bits[0]) - 1;
     if (n1 < 0 || (unsigned long long)n1 > m1 || (unsigned long long)n0 > m0) return 0;
     return column_cells((unsigned long long)n0, (unsigned long long)n1, c2 > 0 ? c2 - 1 : 0,
-                        c2 < m2 ? c2 + 1 : m2, b1, b2, plan, slab_cap, cell_key, slab_lo, slab_hi,
-                        col_lo, col_hi, f);
+                        c2 < m2 ? c2 + 1 : m2, b1, b2, plan, slab_base, nslab, cell_key, slab_lo,
+                        slab_hi, col_lo, col_hi, f);
 }
 
 // Position of the r-th (from 0) set bit of the 8-bit mask m (r < popc(m)).
@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(256, 4)
            const uint32_t *__restrict__ slab_hi, const uint32_t *__restrict__ col_lo,
            const uint32_t *__restrict__ col_hi, const uint8_t *__restrict__ cocc,
            uint32_t *__restrict__ nb_first, uint8_t *__restrict__ nb_cnt,
-           unsigned long long *__restrict__ edge_set, uint32_t edge_set_size)
+           unsigned long long *__restrict__ edge_set, uint32_t edge_set_size,
+           const uint32_t *__restrict__ cframe, const Frame *__restrict__ fr)
 {
     if (call_aborted(&plan->status)) return;
     // the boundary-edge hash set of k_edges starts empty
@@ -318,11 +319,15 @@ __global__ void __launch_bounds__(256, 4)
         const unsigned long long ck = cell_key[c];
         uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int K = 0;
+        // the cell's frame: its part of the slab index; the next cell must be of it too
+        const uint32_t fc = prm.nf > 1 ? cframe[c] : 0u;
+        const uint32_t sbase = fr[fc].slab_base, nslab = fr[fc].nslab;
+        const bool next_same = prm.nf == 1 || (c + 1 < M && cframe[c + 1] == fc);
 #pragma unroll
         for (int col = 0; col < 5; ++col) {
             uint32_t f[3];
-            const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, b1, b2, plan, prm.slab_cap,
-                                        cell_key, slab_lo, slab_hi, col_lo, col_hi, f);
+            const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, b1, b2, plan, sbase, nslab,
+                                        next_same, cell_key, slab_lo, slab_hi, col_lo, col_hi, f);
             for (int t = 0; t < nf; ++t) {
                 const uint32_t q = f[t], first = cell_sc[q];
                 nb_first[(size_t)c * 13 + K] = first;
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
             // region size: kRegionCells, or fewer cells when the cloud has too
             // few cells to give every block two regions
             const uint32_t rc =
-                min((uint32_t)kRegionCells, max(kRegionMinCells, M / (2u * gridDim.x)));
+                min(prm.region_cells, max(kRegionMinCells, M / (2u * gridDim.x)));
             const uint32_t r = atomicAdd(&plan->region_counter, 1u);
             const uint64_t lo = (uint64_t)r * rc;
             S.region = lo < M ? (uint32_t)lo : M;
@@ -921,7 +926,7 @@ __global__ void __launch_bounds__(256, 4)
 // a6: list the kept components (root, smallest index) for the ordering sort.
 __global__ void __launch_bounds__(256)
     k_kept(Plan *plan, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ csize,
-           const uint32_t *__restrict__ cmin, long long min_size, long long max_size,
+           const uint32_t *__restrict__ cmin, Frame *__restrict__ fr, uint32_t nf,
            uint32_t *__restrict__ kept_key, uint32_t *__restrict__ kept_val)
 {
     if (block_aborted(&plan->status)) return;
@@ -932,8 +937,11 @@ __global__ void __launch_bounds__(256)
         const uint32_t a = base + lane;
         bool keep = false;
         if (a < M && parent[a] == a) {
+            // the bounds of the component's frame (the frame of its smallest row)
+            const uint32_t f = frame_of_row(fr, nf, cmin[a]);
             const long long s = (long long)csize[a];
-            keep = s >= min_size && s <= max_size;
+            keep = s >= fr[f].min_size && s <= fr[f].max_size;
+            if (keep && nf > 1) atomicAdd(&fr[f].kept, 1u);
         }
         const uint32_t mask = __ballot_sync(0xffffffffu, keep);
         if (!mask) continue;
@@ -949,15 +957,48 @@ __global__ void __launch_bounds__(256)
 }
 
 // a6: rank of each kept root in smallest-index order.
+// With several frames, kept components are in frame order (their smallest
+// rows are), and each frame numbers its own from 0: rank - the kept
+// components of the frames before it (an exclusive scan every block makes of
+// the frames' kept counts, kMaxFramesPerCall at most).
 __global__ void __launch_bounds__(256)
-    k_rank(Plan *plan, const uint32_t *__restrict__ va, const uint32_t *__restrict__ vb,
-           int32_t *__restrict__ crank)
+    k_rank(Plan *plan, const uint32_t *__restrict__ ka, const uint32_t *__restrict__ kb,
+           const uint32_t *__restrict__ va, const uint32_t *__restrict__ vb, const Frame *__restrict__ fr,
+           uint32_t nf, int32_t *__restrict__ crank)
 {
-    if (call_aborted(&plan->status)) return;
+    __shared__ uint32_t s_base[kMaxFramesPerCall];
+    __shared__ uint32_t s_tot[8];
+    if (block_aborted(&plan->status)) return;
     const uint32_t k = plan->kept.n;
-    const uint32_t *__restrict__ v = (plan->kept.npasses & 1u) ? vb : va;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x)
-        crank[v[t]] = (int32_t)t;
+    const bool in_b = (plan->kept.npasses & 1u) != 0;
+    const uint32_t *__restrict__ v = in_b ? vb : va;
+    const uint32_t *__restrict__ key = in_b ? kb : ka;
+    if (nf > 1) {
+        // exclusive scan of fr[*].kept in chunks of 256 (8 warps)
+        const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < nf; c0 += 256) {
+            const uint32_t f = c0 + t;
+            const uint32_t x = f < nf ? fr[f].kept : 0u;
+            uint32_t incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) s_tot[w] = incl;
+            __syncthreads();
+            uint32_t before = carry;
+            for (int j = 0; j < w; ++j) before += s_tot[j];
+            if (f < nf) s_base[f] = before + incl - x;
+            for (int j = 0; j < 8; ++j) carry += s_tot[j];
+            __syncthreads();
+        }
+    }
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
+        const uint32_t base = nf > 1 ? s_base[frame_of_row(fr, nf, key[t])] : 0u;
+        crank[v[t]] = (int32_t)(t - base);
+    }
 }
 
 // a6: the label of every sub-cell (its root's rank, or -1), written over the
@@ -973,7 +1014,7 @@ __global__ void __launch_bounds__(256)
         sclab[a] = crank[parent[a]];
     // 16-byte stores when the output is 16-byte aligned (a batch frame's
     // labels start anywhere), else 4-byte stores
-    const uint32_t n4 = (reinterpret_cast<uintptr_t>(labels) & 15) ? 0u : n / 4;
+    const uint32_t n4 = (reinterpret_cast<uintptr_t>(labels) & 15) ? 0u : n / 4;  // n: labels to fill
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x)
         __stcs(reinterpret_cast<int4 *>(labels) + q, make_int4(-1, -1, -1, -1));
     for (uint32_t i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -986,7 +1027,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_labels(Plan *plan, const uint32_t *__restrict__ idx_a, const uint32_t *__restrict__ idx_b,
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
-             const int32_t *__restrict__ sclab, int32_t *__restrict__ labels)
+             const int32_t *__restrict__ sclab, int32_t *__restrict__ labels, uint32_t rows)
 {
     if (call_aborted(&plan->status)) return;
     const uint32_t n = plan->sort.n;
@@ -1031,20 +1072,19 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-            if (l[t] >= 0 && i[t] < n) labels[i[t]] = l[t];
+            if (l[t] >= 0 && i[t] < rows) labels[i[t]] = l[t];
     }
     for (uint32_t p = n8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += gridDim.x * blockDim.x) {
         const int32_t l = sclab[sc_of[p]];
         const uint32_t i = idx[(size_t)p * idx_stride];
-        if (l >= 0 && i < n) labels[i] = l;
+        if (l >= 0 && i < rows) labels[i] = l;
     }
 }
 
 }  // namespace
 
-cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
-                          long long max_size, cudaStream_t st)
+cudaError_t enqueue_union(Workspace &ws, const Params &prm, cudaStream_t st)
 {
     const uint32_t qcap = (uint32_t)ws.pairq_cap;
     const uint32_t ecap = (uint32_t)ws.edges_cap;
@@ -1059,7 +1099,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item (cell, sub-cell, edge) per thread
     k_nbrs<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
                                         ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt,
-                                        ws.edge_set, (uint32_t)ws.edge_set_size);
+                                        ws.edge_set, (uint32_t)ws.edge_set_size, ws.cframe, ws.frames);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
     const uint32_t scap = region_scratch(ws, ws.cap_n);
@@ -1085,25 +1125,27 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, long long min_size,
     k_flatten_stats<<<grid1, 256, 0, st>>>(ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
                                                  ws.cmin, prm.union_cap);
     FEC_MARK(ws, "k_flatten_stats", st);
-    k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, min_size, max_size,
-                                        ws.kept_key_a(), ws.kept_val_a());
+    k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, ws.frames, prm.nf,
+                                  ws.kept_key_a(), ws.kept_val_a());
     FEC_MARK(ws, "k_kept", st);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool packed,
+cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bool fill,
                            cudaStream_t st)
 {
     const int grid1 = grid_for(ws, prm.n, 256, 8);
-    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_val_a(), ws.kept_val_b(), ws.crank);
+    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_key_a(), ws.kept_key_b(),
+                                                        ws.kept_val_a(), ws.kept_val_b(), ws.frames,
+                                                        prm.nf, ws.crank);
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
     int32_t *sclab = (int32_t *)ws.csize;  // component sizes are no longer needed
-    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab, labels, prm.n);
+    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab, labels, fill ? prm.rows : 0u);
     FEC_MARK(ws, "k_sclabel", st);
     k_labels<<<grid_for(ws, prm.n, 2048, 8), 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
-                                         (const uint32_t *)ws.vals_b, packed ? 2u : 1u, ws.sc_of,
-                                         sclab, labels);
+                                         (const uint32_t *)ws.vals_b, prm.packed ? 2u : 1u, ws.sc_of,
+                                         sclab, labels, prm.rows);
     FEC_MARK(ws, "k_labels", st);
     return cudaGetLastError();
 }
