@@ -51,9 +51,9 @@ typedef enum {
     FEC_ERR_OOM = 4,            /* workspace above mem_budget_bytes, or cudaMalloc failed */
     FEC_ERR_CUDA = 5,           /* a CUDA runtime call failed */
     FEC_ERR_NOT_CONVERGED = 6,  /* a bounded device loop hit its iteration cap */
-    FEC_ERR_NOT_READY = 7,      /* fec_serve_poll: request still running */
+    FEC_ERR_NOT_READY = 7,      /* fec_serve_poll: request still queued or running */
     FEC_ERR_BUSY = 8,           /* fec_serve_submit: request can never fit the budget / queue full */
-    FEC_ERR_TIMEOUT = 9         /* fec_serve_poll: the wait ended before completion */
+    FEC_ERR_TIMEOUT = 9         /* serving: the request's deadline passed before it started */
 } fec_status;
 
 typedef struct fec_ctx fec_ctx;
@@ -129,22 +129,40 @@ fec_status fec_cluster_batch(fec_ctx *ctx, const float *xyz, const int64_t *offs
                              const float *d, const int64_t *min_size, const int64_t *max_size,
                              int32_t *labels, int32_t *num_clusters);
 
-/* Serving: submit one request.  The input is copied before the call returns;
- * labels_out (host memory, int32 [n]) must stay valid until fec_serve_poll
- * returns a final status for the ticket.  Requests run concurrently on the
- * context's device as workspace slots and the memory budget allow
- * (continuous batching); each result equals fec_cluster on that request
- * alone.  FEC_ERR_BUSY if the request alone exceeds the budget.
+/* Serving: submit one request.  The input is copied into the engine's device
+ * input arena (no device allocation per request): from pageable host memory
+ * the call returns once the copy has been staged, so the caller may reuse
+ * its buffer; from pinned host or device memory the copy runs asynchronously
+ * and the buffer must stay unchanged until fec_serve_poll returns a final
+ * status for the ticket.  labels_out (host memory, int32 [n]) must stay
+ * valid until then too.  Requests
+ * run concurrently on the context's device as workspace slots and the memory
+ * budget allow (continuous batching); each result equals fec_cluster on that
+ * request alone.  Memory: the engine's whole device footprint stays within
+ * the context's budget (40 GiB when it has none): a quarter of it, at most
+ * 2 GiB, is the input arena, the rest the slots' workspaces.
+ * FEC_ERR_BUSY, and no ticket, when the request can never fit the slots'
+ * memory, when 4,096 requests are already waiting, or when the arena has no
+ * room for its input right now (submit again once earlier requests finish).
  * Thread-safe. */
 fec_status fec_serve_submit(fec_ctx *ctx, const float *xyz, int64_t n, float d, int64_t min_size,
                             int64_t max_size, int32_t *labels_out, uint64_t *ticket);
 
+/* Serving: fec_serve_submit with a deadline.  deadline_us > 0: if the
+ * request has not started deadline_us microseconds after submit, it is
+ * dropped without running and completes with FEC_ERR_TIMEOUT (labels_out
+ * untouched); <= 0: no deadline.  Thread-safe. */
+fec_status fec_serve_submit_deadline(fec_ctx *ctx, const float *xyz, int64_t n, float d,
+                                     int64_t min_size, int64_t max_size, int32_t *labels_out,
+                                     int64_t deadline_us, uint64_t *ticket);
+
 /* Serving: wait up to timeout_ms (0 = just check, <0 = forever) for a ticket.
  * FEC_OK: labels_out and *num_clusters are final and the ticket is released.
- * FEC_ERR_NOT_READY (timeout_ms == 0) or FEC_ERR_TIMEOUT (the wait of
- * timeout_ms > 0 ended first): still queued or running; the ticket stays
- * valid.  FEC_ERR_INVALID_ARG: unknown ticket.  Any other status is the
- * request's final error and releases the ticket.  Thread-safe. */
+ * FEC_ERR_NOT_READY: still queued or running when the wait ended; the ticket
+ * stays valid.  FEC_ERR_INVALID_ARG: unknown ticket.  Any other status
+ * (FEC_ERR_TIMEOUT for a request whose deadline passed, or a clustering
+ * error) is the request's final status and releases the ticket.
+ * Thread-safe. */
 fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, int timeout_ms);
 
 /* Serving: fec_serve_poll that also reports when the request completed:
@@ -154,6 +172,23 @@ fec_status fec_serve_poll(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters, 
  * latency independently of how often it polls.  Thread-safe. */
 fec_status fec_serve_poll_timed(fec_ctx *ctx, uint64_t ticket, int32_t *num_clusters,
                                 int timeout_ms, int64_t *done_ns);
+
+/* Serving counters since the engine started (times in nanoseconds). */
+typedef struct {
+    int64_t submitted;         /* requests accepted by submit */
+    int64_t completed;         /* requests that ran (any final status but FEC_ERR_TIMEOUT) */
+    int64_t rejected;          /* submits refused with FEC_ERR_BUSY */
+    int64_t expired;           /* requests dropped at their deadline (FEC_ERR_TIMEOUT) */
+    int64_t queued;            /* requests waiting for a slot now */
+    int64_t queue_max;         /* most requests ever waiting at once */
+    int64_t queue_wait_ns_sum; /* submit -> start, summed over started requests */
+    int64_t queue_wait_ns_max;
+    int64_t run_ns_sum;        /* start -> completion, summed */
+    int64_t run_ns_max;
+    int64_t arena_bytes;       /* size of the device input arena */
+} fec_serve_stats;
+
+fec_status fec_serve_get_stats(fec_ctx *ctx, fec_serve_stats *out);
 
 /* Counters of the last fec_cluster / fec_cluster_batch call on ctx. */
 fec_status fec_get_stats(const fec_ctx *ctx, fec_stats *out);

@@ -373,18 +373,46 @@ struct fec_ctx {
     bool tracing = false;
     uint32_t wait_cap = kWaitCap;    // iteration caps of the device loops (fec_set_iteration_caps)
     uint32_t union_cap = kUnionCap;
+    char *pinned = nullptr;          // pinned staging of pageable inputs and outputs
+    size_t pinned_bytes = 0;
 };
 
 namespace {
 
-bool is_device_ptr(const void *p)
+// Where a caller's buffer lives: device (or managed), pinned host, or
+// pageable host memory.
+enum class Mem { Device, Pinned, Pageable };
+Mem mem_kind(const void *p)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return Mem::Pageable;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return Mem::Device;
+    return a.type == cudaMemoryTypeHost ? Mem::Pinned : Mem::Pageable;
+}
+
+// Pinned staging of at least `bytes` (grown with a quarter of headroom).  A
+// pageable input goes through it: a CPU copy plus an asynchronous DMA
+// instead of the driver's pageable copy path.
+char *pinned_stage(fec_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->pinned_bytes) return ctx->pinned;
+    if (ctx->pinned) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFreeHost(ctx->pinned);
+    }
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    if (cudaMallocHost((void **)&ctx->pinned, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->pinned = nullptr;
+        return nullptr;
+    }
+    ctx->pinned_bytes = want;
+    return ctx->pinned;
 }
 
 fec_status check_args(int64_t n, float d, int64_t min_size, int64_t max_size)
@@ -396,23 +424,39 @@ fec_status check_args(int64_t n, float d, int64_t min_size, int64_t max_size)
 }
 
 // Grow the workspace to hold n points at slab capacity slab_cap.
+// The size a workspace grows to for n points at slab capacity slab_cap: a
+// quarter more points than it holds now (so that slowly growing clouds do
+// not re-allocate every call), or exactly n when that would exceed budget.
+struct Growth {
+    size_t cap, bytes;
+    uint32_t slab;
+};
+Growth growth_for(const Workspace &ws, size_t n, uint32_t slab_cap, size_t budget)
+{
+    Growth g;
+    g.cap = n;
+    if (ws.base && g.cap < ws.cap_n + ws.cap_n / 4) g.cap = ws.cap_n + ws.cap_n / 4;
+    if (g.cap < 4096) g.cap = 4096;
+    g.slab = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
+    Workspace probe;
+    probe.sms = ws.sms;
+    probe.list_scale = ws.list_scale;
+    g.bytes = workspace_layout(probe, nullptr, g.cap, g.slab);
+    if (budget && g.bytes > budget) {
+        g.cap = n < 4096 ? 4096 : n;  // without headroom
+        g.bytes = workspace_layout(probe, nullptr, g.cap, g.slab);
+    }
+    return g;
+}
+
 fec_status ensure_workspace(fec_ctx *ctx, size_t n, uint32_t slab_cap, bool force = false)
 {
     Workspace &ws = ctx->ws;
     if (!force && ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
-    size_t cap = n;
-    if (ws.base && cap < ws.cap_n + ws.cap_n / 4) cap = ws.cap_n + ws.cap_n / 4;
-    if (cap < 4096) cap = 4096;
-    uint32_t sc = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
-    Workspace probe;
-    probe.sms = ws.sms;
-    probe.list_scale = ws.list_scale;
-    size_t bytes = workspace_layout(probe, nullptr, cap, sc);
-    if (ctx->budget && bytes > ctx->budget) {
-        cap = n;  // retry without headroom
-        bytes = workspace_layout(probe, nullptr, cap, sc);
-        if (bytes > ctx->budget) return FEC_ERR_OOM;
-    }
+    const Growth g = growth_for(ws, n, slab_cap, ctx->budget);
+    if (ctx->budget && g.bytes > ctx->budget) return FEC_ERR_OOM;
+    const size_t cap = g.cap, bytes = g.bytes;
+    const uint32_t sc = g.slab;
     // Stream-ordered: the old workspace is released and the new one taken on
     // the context's stream, so growing it stalls no other stream (a plain
     // free would synchronise the whole device).
@@ -492,14 +536,28 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
     ws.trace = ctx->tracing ? &ctx->trace : nullptr;
     if (ws.trace) ws.trace->begin(ctx->stream);
     const float *xin = xyz;
-    if (!is_device_ptr(xyz)) {
-        if (cudaMemcpyAsync(ws.xyz, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream) !=
+    const Mem in_kind = mem_kind(xyz), out_kind = mem_kind(labels);
+    // pinned staging of a pageable input (a pageable output is copied by the
+    // driver: a CPU copy into freshly allocated caller memory would pay its
+    // page faults on the critical path)
+    char *stage = nullptr;
+    if (in_kind == Mem::Pageable) {
+        stage = pinned_stage(ctx, (size_t)n * 12);
+        if (!stage) return FEC_ERR_OOM;
+    }
+    if (in_kind != Mem::Device) {
+        const void *src = xyz;
+        if (in_kind == Mem::Pageable) {
+            std::memcpy(stage, xyz, (size_t)n * 12);
+            src = stage;
+        }
+        if (cudaMemcpyAsync(ws.xyz, src, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream) !=
             cudaSuccess)
             return FEC_ERR_CUDA;
         FEC_MARK(ws, "h2d_xyz", ctx->stream);
         xin = ws.xyz;
     }
-    const bool dev_out = is_device_ptr(labels);
+    const bool dev_out = out_kind == Mem::Device;
     int32_t *lout = dev_out ? labels : ws.labels;
     FrontArgs fa;
     fa.single = true;
@@ -526,21 +584,55 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
 
 size_t ctx_budget(const fec_ctx *ctx) { return ctx->budget; }
 cudaStream_t ctx_stream(const fec_ctx *ctx) { return ctx->stream; }
-// Grows ctx's workspace to n points and a slab index of slab_cap entries
-// when that takes at most max_bytes (a serving slot grows once to the
-// largest request seen so far instead of again at every larger request).
-fec_status ctx_reserve(fec_ctx *ctx, size_t n, uint32_t slab_cap, size_t max_bytes)
-{
-    Workspace &ws = ctx->ws;
-    if (ws.base && n <= ws.cap_n && slab_cap <= ws.slab_cap) return FEC_OK;
-    Workspace probe;
-    probe.sms = ws.sms;
-    probe.list_scale = ws.list_scale;
-    const uint32_t sc = slab_cap > ws.slab_cap ? slab_cap : ws.slab_cap;
-    if (workspace_layout(probe, nullptr, n, sc) > max_bytes) return FEC_OK;
-    return ensure_workspace(ctx, n, slab_cap);
-}
 ServeEngine *ctx_serve(fec_ctx *ctx) { return ctx->serve; }
+int ctx_sms(const fec_ctx *ctx) { return ctx->ws.sms; }
+// Device bytes ctx's workspace holds now.
+size_t ctx_ws_bytes(const fec_ctx *ctx) { return ctx->ws.base ? ctx->ws.bytes : 0; }
+// Bytes it will hold while clustering n points at radius d within budget
+// (its present size when that already fits).
+size_t ctx_projected_bytes(const fec_ctx *ctx, size_t n, float d, size_t budget)
+{
+    const Workspace &ws = ctx->ws;
+    const uint32_t slab = make_params((uint32_t)n, d).slab_cap;
+    if (ws.base && n <= ws.cap_n && slab <= ws.slab_cap) return ws.bytes;
+    return growth_for(ws, n, slab, budget).bytes;
+}
+// Grow ctx's workspace for n points at radius d, within its budget.
+fec_status ctx_grow(fec_ctx *ctx, size_t n, float d)
+{
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaSetDevice(ctx->device);
+    return ensure_workspace(ctx, n, make_params((uint32_t)n, d).slab_cap);
+}
+void ctx_set_budget(fec_ctx *ctx, size_t budget)
+{
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->budget = budget;
+}
+// Release ctx's workspace (after its stream's work); the next call allocates anew.
+void ctx_release_workspace(fec_ctx *ctx)
+{
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Workspace &ws = ctx->ws;
+    if (!ws.base) return;
+    cudaSetDevice(ctx->device);
+    cudaFreeAsync(ws.base, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    ws.base = nullptr;
+    ws.cap_n = 0;
+    ws.bytes = 0;
+    ws.slab_cap = 0;
+}
+
+// Device workspace bytes fec_cluster takes for n points at radius d on a
+// device of `sms` SMs (the region step's scratch scales with the SM count).
+size_t workspace_estimate(int sms, int64_t n, float d)
+{
+    const Params prm = make_params((uint32_t)n, d);
+    Workspace probe;
+    probe.sms = sms > 0 ? sms : 1;
+    return workspace_layout(probe, nullptr, (size_t)(n < 4096 ? 4096 : n), prm.slab_cap);
+}
 
 }  // namespace fec
 
@@ -565,11 +657,15 @@ const char *fec_status_string(fec_status s)
 
 int64_t fec_workspace_bytes(int64_t n, float d)
 {
-    if (n < 0 || !std::isfinite(d) || !(d > 0.0f)) return -1;
-    const Params prm = make_params((uint32_t)n, d);
-    Workspace probe;
-    probe.sms = 160;  // estimate for a device not yet opened
-    return (int64_t)workspace_layout(probe, nullptr, (size_t)(n < 4096 ? 4096 : n), prm.slab_cap);
+    if (n < 0 || n > FEC_MAX_POINTS || !std::isfinite(d) || !(d > 0.0f)) return -1;
+    // the current device's SM count; 160 when no device can be queried
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 160;
+    }
+    return (int64_t)workspace_estimate(sms, n, d);
 }
 
 fec_status fec_create(const fec_options *opt, fec_ctx **out)
@@ -628,6 +724,7 @@ void fec_destroy(fec_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->summary_dev) cudaFree(ctx->summary_dev);
     if (ctx->summary_host) cudaFreeHost(ctx->summary_host);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -4,7 +4,8 @@ Argument marshalling only: every step of the clustering runs in the CUDA
 library.  There is no CPU fallback; if the library is missing this module
 raises on first use.  Functions keep the C names (``fec_create``,
 ``fec_cluster``, ``fec_cluster_batch``, ``fec_serve_submit``,
-``fec_serve_poll``, ``fec_serve_poll_timed``, ``fec_get_stats``, ``fec_workspace_bytes``,
+``fec_serve_poll``, ``fec_serve_poll_timed``, ``fec_serve_submit_deadline``,
+``fec_serve_get_stats``, ``fec_get_stats``, ``fec_workspace_bytes``,
 ``fec_set_iteration_caps``, ``fec_status_string``, ``fec_destroy``) and take raw pointers like the C ABI;
 ``Context`` adds array conveniences on top (numpy arrays = host memory,
 torch CUDA tensors = device memory).
@@ -29,7 +30,8 @@ FEC_OK, FEC_ERR_NOT_READY, FEC_ERR_TIMEOUT = 0, 7, 9
 # Every function the header declares (checked by the CPU tests against include/fec.h).
 EXPORTS = ("fec_create", "fec_destroy", "fec_cluster", "fec_cluster_batch", "fec_serve_submit",
            "fec_serve_poll", "fec_serve_poll_timed", "fec_get_stats", "fec_workspace_bytes", "fec_status_string",
-           "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc", "fec_set_iteration_caps")
+           "fec_trace_enable", "fec_trace_read", "fec_cluster_noalloc", "fec_set_iteration_caps",
+           "fec_serve_submit_deadline", "fec_serve_get_stats")
 FEC_NOALLOC_MAX_POINTS = 32768
 FEC_DEFAULT_WAIT_CAP = 1 << 22
 FEC_DEFAULT_UNION_CAP = 1 << 20
@@ -55,6 +57,15 @@ class fec_stats(ctypes.Structure):
                 ("pair_box_joins", ctypes.c_int64), ("pair_point_tests", ctypes.c_int64),
                 ("pair_same_root", ctypes.c_int64), ("point_evals", ctypes.c_int64),
                 ("pairs_queued", ctypes.c_int64), ("boundary_edges", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fec_serve_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "rejected", "expired", "queued", "queue_max", "queue_wait_ns_sum",
+        "queue_wait_ns_max", "run_ns_sum", "run_ns_max", "arena_bytes")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +104,11 @@ def load(build_if_missing: bool = False):
     lib.fec_serve_submit.argtypes = [vp, f32p, i64, ctypes.c_float, i64, i64, vp,
                                      ctypes.POINTER(ctypes.c_uint64)]
     lib.fec_serve_submit.restype = ctypes.c_int
+    lib.fec_serve_submit_deadline.argtypes = [vp, f32p, i64, ctypes.c_float, i64, i64, vp, i64,
+                                              ctypes.POINTER(ctypes.c_uint64)]
+    lib.fec_serve_submit_deadline.restype = ctypes.c_int
+    lib.fec_serve_get_stats.argtypes = [vp, ctypes.POINTER(fec_serve_stats)]
+    lib.fec_serve_get_stats.restype = ctypes.c_int
     lib.fec_serve_poll.argtypes = [vp, ctypes.c_uint64, i32p, ctypes.c_int]
     lib.fec_serve_poll.restype = ctypes.c_int
     lib.fec_serve_poll_timed.argtypes = [vp, ctypes.c_uint64, i32p, ctypes.c_int,
@@ -163,6 +179,23 @@ def fec_serve_submit(ctx, xyz_ptr, n, d, min_size, max_size, labels_ptr) -> tupl
     st = load().fec_serve_submit(ctx, xyz_ptr, int(n), float(d), int(min_size), int(max_size),
                                  labels_ptr, ctypes.byref(t))
     return st, t.value
+
+
+def fec_serve_submit_deadline(ctx, xyz_ptr, n, d, min_size, max_size, labels_ptr,
+                              deadline_us) -> tuple[int, int]:
+    t = ctypes.c_uint64(0)
+    st = load().fec_serve_submit_deadline(ctx, xyz_ptr, int(n), float(d), int(min_size),
+                                          int(max_size), labels_ptr, int(deadline_us),
+                                          ctypes.byref(t))
+    return st, t.value
+
+
+def fec_serve_get_stats(ctx) -> dict:
+    s = fec_serve_stats()
+    st = load().fec_serve_get_stats(ctx, ctypes.byref(s))
+    if st != FEC_OK:
+        raise FecError(st, "fec_serve_get_stats")
+    return s.as_dict()
 
 
 def fec_serve_poll(ctx, ticket, timeout_ms=-1) -> tuple[int, int]:
@@ -295,17 +328,21 @@ class Context:
             raise FecError(st, "fec_cluster_batch")
         return labels, ks[:nb]
 
-    def submit(self, xyz, d, min_size, max_size, labels_out):
+    def submit(self, xyz, d, min_size, max_size, labels_out, deadline_us=0):
         xyz = np.ascontiguousarray(xyz, dtype=np.float32)
-        st, t = fec_serve_submit(self.handle, xyz.ctypes.data, xyz.size // 3, d, min_size, max_size,
-                                 labels_out.ctypes.data)
+        st, t = fec_serve_submit_deadline(self.handle, xyz.ctypes.data, xyz.size // 3, d, min_size,
+                                          max_size, labels_out.ctypes.data, deadline_us)
         if st != FEC_OK:
             raise FecError(st, "fec_serve_submit")
         return t
 
     def poll(self, ticket, timeout_ms=-1):
-        """(status, k).  Status FEC_OK, or NOT_READY / TIMEOUT while running."""
+        """(status, k).  Status FEC_OK, NOT_READY while queued or running, or
+        a final error (TIMEOUT: the request's deadline passed first)."""
         return fec_serve_poll(self.handle, ticket, timeout_ms)
+
+    def serve_stats(self) -> dict:
+        return fec_serve_get_stats(self.handle)
 
     def poll_timed(self, ticket, timeout_ms=-1):
         """(status, k, done_ns): done_ns = CLOCK_MONOTONIC completion time."""

@@ -135,3 +135,67 @@ def test_serve_rejects_over_budget():
         with pytest.raises(fec.FecError) as e:
             srv.submit(xyz, 0.3, 1, 10, np.zeros(100_000, np.int32))
         assert e.value.name == "FEC_ERR_BUSY"
+
+
+def test_serve_deadline_drops_requests_that_cannot_start():
+    """A request whose deadline passes before a slot takes it completes with
+    FEC_ERR_TIMEOUT without running (labels untouched); the requests around
+    it are unaffected."""
+    big = [synth.serve_request(5, i, lo=300_000, hi=400_000) for i in range(6)]
+    small = synth.serve_request(5, 20, lo=5_000, hi=6_000)
+    with fec.Context(device=0) as srv, fec.Context(device=0) as solo:
+        outs = [np.full(r.n, -7, np.int32) for r in big]
+        tickets = [srv.submit(r.xyz, r.d, r.min_size, r.max_size, o) for r, o in zip(big, outs)]
+        late = np.full(small.n, -7, np.int32)
+        t_late = srv.submit(small.xyz, small.d, small.min_size, small.max_size, late, deadline_us=1)
+        st, _ = srv.poll(t_late, -1)
+        assert fec.STATUS[st] == "FEC_ERR_TIMEOUT"
+        assert np.all(late == -7)
+        for r, o, t in zip(big, outs, tickets):
+            st, k = srv.poll(t, -1)
+            assert st == fec.FEC_OK
+            alone, k_alone = solo.cluster(r.xyz, r.d, r.min_size, r.max_size)
+            assert k == k_alone
+            np.testing.assert_array_equal(o, alone)
+        # a generous deadline does not drop anything
+        ok = np.full(small.n, -7, np.int32)
+        t_ok = srv.submit(small.xyz, small.d, small.min_size, small.max_size, ok, deadline_us=10_000_000)
+        st, k = srv.poll(t_ok, -1)
+        assert st == fec.FEC_OK
+        want, kw = oracle.cluster(small.xyz, small.d, small.min_size, small.max_size)
+        assert k == kw
+        np.testing.assert_array_equal(ok, want)
+        s = srv.serve_stats()
+        assert s["expired"] == 1 and s["completed"] == 7 and s["submitted"] == 8
+
+
+def test_serve_queue_full_is_busy_and_accepted_requests_are_exact():
+    """With a 64 MiB budget the input arena holds about eleven 120k-point
+    inputs and only one request runs at a time; forty submits in a row from
+    device memory fill the arena, and the surplus is refused with
+    FEC_ERR_BUSY (no ticket).  Every accepted request is exact."""
+    import torch
+
+    c = synth.frame_120k()
+    want, kw = oracle.cluster(c.xyz, c.d, c.min_size, c.max_size)
+    x = torch.from_numpy(c.xyz).cuda()
+    torch.cuda.synchronize()
+    with fec.Context(device=0, mem_budget_bytes=64 << 20) as srv:
+        outs, tickets, busy = [], [], 0
+        for _ in range(40):
+            o = np.full(c.n, -7, np.int32)
+            st, t = fec.fec_serve_submit(srv.handle, x.data_ptr(), c.n, c.d, c.min_size, c.max_size,
+                                         o.ctypes.data)
+            if fec.STATUS[st] == "FEC_ERR_BUSY":
+                busy += 1
+                continue
+            assert st == fec.FEC_OK
+            outs.append(o)
+            tickets.append(t)
+        for o, t in zip(outs, tickets):
+            st, k = srv.poll(t, -1)
+            assert st == fec.FEC_OK and k == kw
+            np.testing.assert_array_equal(o, want)
+        s = srv.serve_stats()
+        assert busy >= 1 and s["rejected"] == busy
+        assert s["arena_bytes"] == 16 << 20 and s["queue_max"] >= 2
