@@ -75,11 +75,6 @@ int max_sort_passes(const Params &prm)
     return (bits + kRadixBits - 1) / kRadixBits;
 }
 
-int kept_sort_passes(uint32_t n)
-{
-    const int b = n > 1 ? bitlen_host(n - 1) : 0;
-    return (b + kRadixBits - 1) / kRadixBits;
-}
 
 // ---------------------------------------------------------------------------
 // Workspace
@@ -140,6 +135,10 @@ size_t workspace_layout(Workspace &ws, void *base, size_t cap_n, uint32_t slab_c
     while (es < n / 8) es <<= 1;
     ws.edge_set_size = es;
     ws.edge_set = (unsigned long long *)take(sizeof(unsigned long long) * es);
+    const size_t words = n / 32 + 1;
+    ws.rank_bits = (uint32_t *)take(4 * words);
+    ws.rank_prefix = (uint32_t *)take(4 * words);
+    ws.rank_status = (unsigned long long *)take(8 * (words / 2048 + 2));
     ws.nb_first = (uint32_t *)take(4 * 13 * n);
     ws.nb_cnt = (uint8_t *)take(32 * n);
     ws.scratch_words = (size_t)region_grid(ws, n) * region_scratch(ws, n);
@@ -164,18 +163,31 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm_i
 {
     Params prm = prm_in;
     prm.col_bits = ws.col_bits;
-    const uint32_t n = prm.n;
-    const int sort_grid = ws.sms;  // per SM; the sort multiplies by its occupancy
     cudaError_t e = enqueue_front(ws, xyz, prm, fa, st);
     if (e != cudaSuccess) return e;
-    // a2: both key widths are enqueued; the plan enables one of them.
+    return enqueue_back(ws, xyz, prm, labels, fill_labels, st);
+}
+
+cudaError_t enqueue_back(Workspace &ws, const float *xyz, const Params &prm_in, int32_t *labels,
+                         bool fill_labels, cudaStream_t st, const KeyLayout *known)
+{
+    Params prm = prm_in;
+    prm.col_bits = ws.col_bits;
+    const int sort_grid = ws.sms;  // per SM; the sort multiplies by its occupancy
+    cudaError_t e = cudaSuccess;
+    // a2: the passes of the width the plan selected, when the host knows it;
+    // else both key widths (the kernels of the other width return at once)
     const bool pk = prm.packed != 0;
-    e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b, ws.vals_b,
-                    false, pk, !pk, ws.sort_status, prm.ntiles, 4, sort_grid, st, &ws.plan->status,
-                    main_sort_source(ws, xyz, prm));
-    if (e != cudaSuccess) return e;
-    const int p64 = max_sort_passes(prm);
-    if (p64 > 4) {
+    const bool run32 = !known || !known->key64, run64 = !known || known->key64;
+    const int p64 = known ? known->passes : max_sort_passes(prm);
+    if (run32) {
+        e = launch_sort(ws, "onesweep_u32", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
+                        ws.vals_b, false, pk, !pk, ws.sort_status, prm.ntiles,
+                        known ? known->passes : 4, sort_grid, st, &ws.plan->status,
+                        main_sort_source(ws, xyz, prm));
+        if (e != cudaSuccess) return e;
+    }
+    if (run64 && p64 > 4) {
         e = launch_sort(ws, "onesweep_u64", &ws.plan->sort, ws.keys_a, ws.vals_a, ws.keys_b,
                         ws.vals_b, true, pk, !pk, ws.sort_status, prm.ntiles, p64, sort_grid, st,
                         &ws.plan->status, main_sort_source(ws, xyz, prm));
@@ -185,17 +197,6 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm_i
     if (e != cudaSuccess) return e;
     e = enqueue_union(ws, prm, st);
     if (e != cudaSuccess) return e;
-    // kept components by their smallest input row (rows < prm.rows)
-    const int kp = kept_sort_passes(prm.rows);
-    if (kp > 0) {
-        e = launch_hist_u32(&ws.plan->kept, ws.kept_key_a(), &ws.plan->status, ws.sms * 4, st);
-        if (e != cudaSuccess) return e;
-        FEC_MARK(ws, "hist_kept", st);
-        e = launch_sort(ws, "onesweep_kept", &ws.plan->kept, ws.kept_key_a(), ws.kept_val_a(),
-                        ws.kept_key_b(), ws.kept_val_b(), false, false, false, ws.sort_status,
-                        frame_tiles(n), kp, sort_grid, st, &ws.plan->status);
-        if (e != cudaSuccess) return e;
-    }
     return enqueue_labels(ws, prm, labels, fill_labels, st);
 }
 
@@ -203,6 +204,7 @@ cudaError_t enqueue_cluster(Workspace &ws, const float *xyz, const Params &prm_i
 struct Summary {
     uint32_t status, k, M_s, M_c, key_bits, pad[3];
     unsigned long long ctr[8];
+    uint32_t front[4];  // the plan's front[] (read back after k_plan)
 };
 
 __global__ void k_summary(const Plan *plan, Summary *out)
@@ -563,8 +565,29 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
     fa.single = true;
     fa.min_size = min_size;
     fa.max_size = max_size;
-    if (enqueue_cluster(ws, xin, prm, fa, lout, true, ctx->stream) != cudaSuccess)
+    Params pc = prm;
+    pc.col_bits = ws.col_bits;
+    if (enqueue_front(ws, xin, pc, fa, ctx->stream) != cudaSuccess) return FEC_ERR_CUDA;
+    // The plan's outcome back on the host (16 bytes): a data error ends the
+    // call here, and the sort launches exactly the passes of the key width
+    // the plan selected (no launches that would only return).
+    uint32_t *front = ctx->summary_host->front;
+    if (cudaMemcpyAsync(front, ws.plan->front, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return FEC_ERR_CUDA;
+    if (front[0] & (ST_NONFINITE | ST_OUT_OF_RANGE | ST_KEY_OVERFLOW | ST_SIZE_OVERFLOW)) {
+        if (ws.trace) ws.trace->end();
+        ws.trace = nullptr;
+        ctx->summary_host->status = front[0];
+        ctx->last = fec_stats{};
+        ctx->last.n = n;
+        return status_from_bits(front[0]);
+    }
+    KeyLayout kl;
+    kl.key64 = front[1] != 0;
+    kl.passes = (int)front[2];
+    if (enqueue_back(ws, xin, pc, lout, true, ctx->stream, &kl) != cudaSuccess) return FEC_ERR_CUDA;
     if (!dev_out) {
         if (cudaMemcpyAsync(labels, ws.labels, (size_t)n * 4, cudaMemcpyDeviceToHost,
                             ctx->stream) != cudaSuccess)

@@ -40,8 +40,7 @@ __device__ __forceinline__ T warp_max(T v)
 // device fields and per-frame histograms).  A single cloud (single = 1)
 // also gets its one frame's static fields here, so it needs no upload.
 __global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint32_t n,
-                       uint32_t kept_passes, uint32_t wait_cap, int single, long long min_size,
-                       long long max_size)
+                       uint32_t wait_cap, int single, long long min_size, long long max_size)
 {
     const int t = threadIdx.x;
     if (blockIdx.x == 0) {
@@ -62,6 +61,7 @@ __global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint
             plan->edges_n = 0;
             plan->region_counter = 0;
             plan->slab_need = 0;
+            plan->rank_tile_counter = 0;
             plan->sort.n = n;
             plan->sort.npasses = 0;
             plan->sort.key64 = 0;
@@ -69,7 +69,7 @@ __global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint
             plan->sort.wait_cap = wait_cap;
             plan->kept.wait_cap = wait_cap;
             plan->kept.n = 0;
-            plan->kept.npasses = kept_passes;
+            plan->kept.npasses = 0;
             plan->kept.key64 = 0;
             plan->kept.parity = 0;
         }
@@ -268,8 +268,18 @@ __global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr
     if (t < 3) s_cm[t] = 0;
     if (t == 0) s_stop = (plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) ? 1u : 0u;
     __syncthreads();
+    // the host's 16-byte read-back of the outcome
+    auto publish = [&]() {
+        plan->front[0] = plan->status;
+        plan->front[1] = plan->sort.key64;
+        plan->front[2] = plan->sort.npasses;
+        plan->front[3] = plan->key_bits;
+    };
     if (s_stop) {
-        if (t == 0) plan->sort.n = 0;
+        if (t == 0) {
+            plan->sort.n = 0;
+            publish();
+        }
         return;
     }
     for (uint32_t f = t; f < prm.nf; f += blockDim.x)
@@ -297,13 +307,13 @@ __global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr
             plan->status |= ST_KEY_OVERFLOW;
             plan->sort.n = 0;
             s_stop = 1;
+            publish();
         } else {
             plan->key_bits = total + 3;
             plan->use_cols =
                 (prm.nf == 1 && plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
             plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
             plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
-            plan->kept.parity = plan->sort.npasses & 1u;  // the look-back array the main sort leaves clear
         }
     }
     __syncthreads();
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr
             plan->status |= ST_SIZE_OVERFLOW;
             plan->sort.n = 0;
         }
+        publish();
     }
 }
 
@@ -348,6 +359,11 @@ struct Clears {
     size_t scan_words;
     uint32_t *slab_lo, *slab_hi;    // slab index
     size_t slab_words;
+    uint32_t *col_lo, *col_hi;      // dense column index (size from the plan)
+    uint32_t *rank_bits;            // kept-component bitmap
+    size_t rank_words;
+    unsigned long long *rank_status;  // its scan's look-back
+    size_t rank_status_words;
     size_t max_words;
 };
 
@@ -373,6 +389,17 @@ __device__ __forceinline__ void keys_body(const float *__restrict__ xyz, Plan *p
         if (i < clr.slab_words) {
             clr.slab_lo[i] = 0;
             clr.slab_hi[i] = 0;
+        }
+        if (i < clr.rank_words) clr.rank_bits[i] = 0;
+        if (i < clr.rank_status_words) clr.rank_status[i] = 0;
+    }
+    // the dense column index, when the plan uses it (its size is known now)
+    if (plan->use_cols) {
+        const size_t ncol = (size_t)1 << (plan->bits[0] + plan->bits[1]);
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ncol;
+             i += (size_t)gridDim.x * blockDim.x) {
+            clr.col_lo[i] = 0;
+            clr.col_hi[i] = 0;
         }
     }
     const int np = (int)ctl->npasses;
@@ -845,19 +872,19 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// a3: the same for the queued sub-cells of kBigSubcell..kHugeSubcell points,
-// one warp per sub-cell.
-__global__ void __launch_bounds__(256)
-    k_subcell_big(Plan *plan, Params prm, const Rec *__restrict__ rec,
-                  const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
-                  const Frame *__restrict__ fr)
+// a3: the same for the queued sub-cells of big_subcell..kHugeSubcell points,
+// one warp per sub-cell (block `blk` of `nblk` blocks doing this part).
+__device__ __forceinline__ void subcell_big(Plan *plan, const Params &prm, const Rec *__restrict__ rec,
+                                            const uint32_t *__restrict__ sc_start,
+                                            const uint32_t *__restrict__ big, SubBox *__restrict__ box,
+                                            uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
+                                            const Frame *__restrict__ fr, uint32_t blk, uint32_t nblk)
 {
     if (call_aborted(&plan->status)) return;
     const uint32_t nb = plan->n_big;
     const int l = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < nb; j += nwarps) {
+    const uint32_t nwarps = nblk * (blockDim.x >> 5);
+    for (uint32_t j = blk * (blockDim.x >> 5) + (threadIdx.x >> 5); j < nb; j += nwarps) {
         const uint32_t a = big[j];
         const uint32_t s = sc_start[a], e = sc_start[a + 1];
         const Rec r0 = rec[s];
@@ -903,13 +930,13 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// a3: the same for the queued sub-cells above kHugeSubcell points, one block per
-// sub-cell.
-__global__ void __launch_bounds__(256)
-    k_subcell_huge(Plan *plan, Params prm, const Rec *__restrict__ rec,
-                  const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
-                  SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
-                  const Frame *__restrict__ fr)
+// a3: the same for the queued sub-cells above kHugeSubcell points, one block
+// per sub-cell (block `blk` of `nblk` blocks doing this part).
+__device__ __forceinline__ void subcell_huge(Plan *plan, const Params &prm, const Rec *__restrict__ rec,
+                                             const uint32_t *__restrict__ sc_start,
+                                             const uint32_t *__restrict__ big, SubBox *__restrict__ box,
+                                             uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
+                                             const Frame *__restrict__ fr, uint32_t blk, uint32_t nblk)
 {
     __shared__ int32_t s_v[7][8];
     __shared__ unsigned long long s_k[8];
@@ -917,7 +944,7 @@ __global__ void __launch_bounds__(256)
     const uint32_t nb = plan->n_huge;
     big += plan->sort.n / 2;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (uint32_t j = blockIdx.x; j < nb; j += gridDim.x) {
+    for (uint32_t j = blk; j < nb; j += nblk) {
         const uint32_t a = big[j];
         const uint32_t s = sc_start[a], e = sc_start[a + 1];
         const Rec r0 = rec[s];
@@ -984,21 +1011,24 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// a3: the large sub-cells, in one launch: the first `huge_blocks` blocks take
+// the huge ones (a block each), the rest the big ones (a warp each).
+__global__ void __launch_bounds__(256)
+    k_subcell_large(Plan *plan, Params prm, const Rec *__restrict__ rec,
+                    const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ big,
+                    SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
+                    const Frame *__restrict__ fr, uint32_t huge_blocks)
+{
+    if (blockIdx.x < huge_blocks)
+        subcell_huge(plan, prm, rec, sc_start, big, box, sminidx, reps, fr, blockIdx.x, huge_blocks);
+    else
+        subcell_big(plan, prm, rec, sc_start, big, box, sminidx, reps, fr, blockIdx.x - huge_blocks,
+                    gridDim.x - huge_blocks);
+}
+
 // a3: slab index over the major cell coordinate: cells of slab x occupy
 // [slab_lo[x], slab_hi[x]) of the sorted cell array (empty: lo == hi == 0);
 // and, when it fits, the dense column index over (c_p0, c_p1) the same way.
-__global__ void __launch_bounds__(256)
-    k_clear_cols(Plan *plan, uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi)
-{
-    if (!plan->use_cols || call_aborted(&plan->status)) return;
-    const size_t ncol = (size_t)1 << (plan->bits[0] + plan->bits[1]);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ncol;
-         i += (size_t)gridDim.x * blockDim.x) {
-        col_lo[i] = 0;
-        col_hi[i] = 0;
-    }
-}
-
 __global__ void __launch_bounds__(256)
     k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
             const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
@@ -1049,8 +1079,8 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, co
     const uint64_t hist_words = (uint64_t)prm.nf * kMaxPasses * kRadixBins;
     const int igrid = (int)std::min<uint64_t>((hist_words + 2047) / 2048, (uint64_t)ws.sms * 4);
     k_init<<<igrid < 1 ? 1 : igrid, 256, 0, st>>>(ws.plan, ws.frames, prm.nf, ws.fhist, prm.n,
-                                                  (uint32_t)kept_sort_passes(prm.rows), prm.wait_cap,
-                                                  fa.single ? 1 : 0, fa.min_size, fa.max_size);
+                                                  prm.wait_cap, fa.single ? 1 : 0, fa.min_size,
+                                                  fa.max_size);
     FEC_MARK(ws, "k_init", st);
     if (multi) k_bbox<true><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
     else k_bbox<false><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
@@ -1065,8 +1095,13 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, co
     clr.slab_lo = ws.slab_lo;
     clr.slab_hi = ws.slab_hi;
     clr.slab_words = prm.slab_cap;
-    clr.max_words = clr.sort_words > clr.scan_words ? clr.sort_words : clr.scan_words;
-    if (clr.slab_words > clr.max_words) clr.max_words = clr.slab_words;
+    clr.col_lo = ws.col_lo;
+    clr.col_hi = ws.col_hi;
+    clr.rank_bits = ws.rank_bits;
+    clr.rank_words = ((size_t)prm.n + 31) / 32;
+    clr.rank_status = ws.rank_status;
+    clr.rank_status_words = clr.rank_words / 2048 + 2;
+    clr.max_words = std::max({clr.sort_words, clr.scan_words, clr.slab_words, clr.rank_words});
     // packed layout: the sort's first pass computes the keys itself
     if (prm.packed && !multi)
         k_keys<false, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
@@ -1107,16 +1142,12 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps,
                                            ws.frames);
     FEC_MARK(ws, "k_subcell_stats", st);
-    k_subcell_big<<<grid_for(ws, prm.n / (prm.big_subcell + 1), 8, 4), 256, 0, st>>>(
-        ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box, ws.sminidx, ws.reps, ws.frames);
-    FEC_MARK(ws, "k_subcell_big", st);
-    k_subcell_huge<<<grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2), 256, 0, st>>>(
-        ws.plan, prm, ws.rec, ws.sc_start, ws.big, ws.box, ws.sminidx, ws.reps, ws.frames);
-    FEC_MARK(ws, "k_subcell_huge", st);
-    if (prm.nf == 1) {  // the dense column index serves single clouds only
-        k_clear_cols<<<ws.sms * 8, 256, 0, st>>>(ws.plan, ws.col_lo, ws.col_hi);
-        FEC_MARK(ws, "k_clear_cols", st);
-    }
+    const int huge_blocks = grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2);
+    const int big_blocks = grid_for(ws, prm.n / (prm.big_subcell + 1), 8, 4);
+    k_subcell_large<<<huge_blocks + big_blocks, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big,
+                                                             ws.box, ws.sminidx, ws.reps, ws.frames,
+                                                             (uint32_t)huge_blocks);
+    FEC_MARK(ws, "k_subcell_large", st);
     k_slabs<<<grid1, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
                                   ws.col_lo, ws.col_hi, ws.cocc, ws.cframe, ws.frames, prm.nf);
     FEC_MARK(ws, "k_slabs", st);

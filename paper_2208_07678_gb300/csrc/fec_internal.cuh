@@ -158,6 +158,10 @@ __device__ __forceinline__ uint32_t frame_of_tile(const Frame *fr, uint32_t nf, 
 
 // Per-call plan (device memory), written by k_plan / k_cells / kernels.
 struct Plan {
+    // written by k_plan for the host: status, key64, passes of the main
+    // sort, key bits (one 16-byte read-back decides which sort passes to
+    // launch)
+    uint32_t front[4];
     int32_t perm[3];           // permuted axis p -> original axis (p0 major .. p2 minor)
     uint32_t bits[3];          // bits of the cell coordinate per permuted axis
     uint32_t key_bits;         // total sort-key bits (cell key bits + 3)
@@ -171,9 +175,10 @@ struct Plan {
     uint32_t edges_n;           // boundary edges emitted by the neighbour step
     uint32_t region_counter;    // dynamic regions of the neighbour step
     uint32_t slab_need;         // slab-index entries the frames need (all frames)
+    uint32_t rank_tile_counter; // dynamic tiles of the kept-component ranking scan
     unsigned long long ctr[8];  // work counters of the union step (CTR_*)
     SortCtl sort;              // main (key, index) sort
-    SortCtl kept;              // sort of kept components by smallest index
+    SortCtl kept;              // kept components: kept.n is their count
 };
 
 // Host-side constants of one call, passed by value.
@@ -475,15 +480,16 @@ struct Workspace {
     size_t edge_set_size = 0;
     uint32_t *nb_first = nullptr;  // per cell: first sub-cell of each neighbour cell (13)
     uint8_t *nb_cnt = nullptr;     // per cell, 32 bytes: neighbour occupancies and offsets
+    uint32_t *rank_bits = nullptr;   // bitmap over positions: smallest rows of kept components
+    uint32_t *rank_prefix = nullptr; // per bitmap word: set bits before it
+    unsigned long long *rank_status = nullptr;  // look-back status of the ranking scan
     uint32_t *scratch = nullptr;   // per block of the neighbour step: undecided in-region pairs
     size_t scratch_words = 0;
     uint32_t list_scale = 1;       // boundary-edge and pair lists hold list_scale * 2 * cap_n
     size_t pairq_cap = 0;
-    // The kept-component sort reuses the key buffers once the cell table is built.
+    // The kept-component list reuses the key buffers once the cell table is built.
     uint32_t *kept_key_a() const { return (uint32_t *)keys_a; }
     uint32_t *kept_val_a() const { return (uint32_t *)keys_a + cap_n; }
-    uint32_t *kept_key_b() const { return (uint32_t *)keys_b; }
-    uint32_t *kept_val_b() const { return (uint32_t *)keys_b + cap_n; }
 };
 
 // Record a trace mark named `name` after the launch just enqueued on st
@@ -540,8 +546,6 @@ inline uint32_t max_tiles(size_t cap_n, uint32_t nf_cap)
 Params make_params(uint32_t n, float d);
 // Upper bound of 8-bit passes of the main sort over any cloud at this S.
 int max_sort_passes(const Params &prm);
-// Passes of the kept-component sort (keys are point indices < n).
-int kept_sort_passes(uint32_t n);
 
 // How a call's frame table is set: by k_init for a single cloud (single =
 // true, with its size bounds), else uploaded by the host before the call.
@@ -552,6 +556,16 @@ struct FrontArgs {
 // a1 (init, bbox, plan, keys) for the call's prm.n points at xyz (device).
 cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, const FrontArgs &fa,
                           cudaStream_t st);
+// The main sort's key layout, when the host has read it back from the plan:
+// only its passes of its width are launched (else both widths are launched
+// and the kernels of the width the plan does not select return at once).
+struct KeyLayout {
+    bool key64 = false;
+    int passes = 0;
+};
+// Everything after enqueue_front (a2 .. a6).
+cudaError_t enqueue_back(Workspace &ws, const float *xyz, const Params &prm, int32_t *labels,
+                         bool fill_labels, cudaStream_t st, const KeyLayout *known = nullptr);
 // a3 (cell table, sub-cell stats, slab index).
 cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cudaStream_t st);
 // a4 + a5 + kept list of a6 (size bounds from the frame table).
@@ -619,9 +633,6 @@ inline size_t sort_status_words(uint32_t tiles)
 {
     return 2 * ((size_t)tiles + 1) * kRadixBins;
 }
-// Digit histograms of all passes for 32-bit keys already in memory.
-cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, const uint32_t *status, int grid,
-                            cudaStream_t st);
 
 int sm_count();
 

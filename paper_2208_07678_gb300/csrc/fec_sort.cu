@@ -72,8 +72,8 @@ __device__ __forceinline__ void scan256(const uint32_t *in, uint32_t *out, uint3
 // on its own, in its own positions: tiles never straddle two frames, a tile's
 // digit offsets come from its frame's histograms, and the look-back stops at
 // the frame's first tile.  Otherwise one run of ctl->n keys: the main sort
-// of one frame (fr non-null: its histograms and input rows), or the
-// kept-component sort (fr null: histograms in ctl).  Values of a first pass
+// of one frame (fr non-null: its histograms and input rows), or a plain
+// sort of ctl->n keys (fr null: histograms in ctl).  Values of a first pass
 // that has none are the points' input rows.
 template <typename KeyT, typename ValT, bool XYZ, bool SEG>
 __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
@@ -278,28 +278,6 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
     }
 }
 
-// Digit histograms of every pass for 32-bit keys (count read from ctl).
-__global__ void __launch_bounds__(256) k_hist_u32(SortCtl *__restrict__ ctl,
-                                                   const uint32_t *__restrict__ keys,
-                                                   const uint32_t *__restrict__ status)
-{
-    __shared__ uint32_t h[4][kRadixBins];
-    if (block_aborted(status)) return;
-    const uint32_t n = ctl->n;
-    const int np = min((int)ctl->npasses, 4);
-    for (int i = threadIdx.x; i < 4 * kRadixBins; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        for (int p = 0; p < np; ++p) atomicAdd(&h[p][(k >> (p * kRadixBits)) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < np * kRadixBins; i += blockDim.x) {
-        const uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(&ctl->hist[i / kRadixBins][i % kRadixBins], v);
-    }
-}
-
 template <typename KeyT, typename ValT>
 cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, void *ka_, void *va_,
                           void *kb_, void *vb_, bool identity_vals, uint32_t *tile_status,
@@ -338,8 +316,7 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
     if (grid > (int)tiles) grid = tiles > 0 ? (int)tiles : 1;  // a small sort needs fewer blocks
     // The look-back array the first pass uses is clear on entry: the key
     // kernel clears array 0 before the main sort, and every pass clears its
-    // tiles' slots in the other array for the next pass, so after the main
-    // sort the array its pass count points at is clear for the kept sort.
+    // tiles' slots in the other array for the next pass.
     const size_t tstride = sort_tstride(ws);
     cudaError_t e = cudaSuccess;
     KeyT *kin = (KeyT *)ka_, *kout = (KeyT *)kb_;
@@ -402,13 +379,6 @@ cudaError_t launch_sort(const Workspace &ws, const char *name, SortCtl *ctl, voi
                                        tile_status, tiles, max_passes, grid, st, status, src);
     return launch_sort_t<u64, u64>(ws, name, ctl, keys_a, vals_a, keys_b, vals_b, identity_vals,
                                    tile_status, tiles, max_passes, grid, st, status, src);
-}
-
-cudaError_t launch_hist_u32(SortCtl *ctl, const uint32_t *keys, const uint32_t *status, int grid,
-                            cudaStream_t st)
-{
-    k_hist_u32<<<grid, 256, 0, st>>>(ctl, keys, status);
-    return cudaGetLastError();
 }
 
 }  // namespace fec

@@ -923,11 +923,20 @@ __global__ void __launch_bounds__(256, 4)
     }
 }
 
-// a6: list the kept components (root, smallest index) for the ordering sort.
+// a6: numbering of the kept components by their smallest point index,
+// without sorting them: each kept component sets one bit at the sorted
+// position of its smallest input row (position order is row order within a
+// frame, and frames are in row order), a scan counts the set bits before
+// every bitmap word, and a component's number is the count of set bits
+// before its own (minus those before its frame's first position).
+//
+// k_kept: list the kept components (position of the smallest row, root),
+// set their bits, count them (per frame too).
 __global__ void __launch_bounds__(256)
     k_kept(Plan *plan, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ csize,
            const uint32_t *__restrict__ cmin, Frame *__restrict__ fr, uint32_t nf,
-           uint32_t *__restrict__ kept_key, uint32_t *__restrict__ kept_val)
+           uint32_t *__restrict__ kept_key, uint32_t *__restrict__ kept_val,
+           uint32_t *__restrict__ rank_bits)
 {
     if (block_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
@@ -936,12 +945,18 @@ __global__ void __launch_bounds__(256)
     for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < M; base += stride) {
         const uint32_t a = base + lane;
         bool keep = false;
+        uint32_t pos = 0;
         if (a < M && parent[a] == a) {
             // the bounds of the component's frame (the frame of its smallest row)
-            const uint32_t f = frame_of_row(fr, nf, cmin[a]);
+            const uint32_t row = cmin[a];
+            const uint32_t f = frame_of_row(fr, nf, row);
             const long long s = (long long)csize[a];
             keep = s >= fr[f].min_size && s <= fr[f].max_size;
-            if (keep && nf > 1) atomicAdd(&fr[f].kept, 1u);
+            pos = fr[f].pos_off + (row - fr[f].in_off);
+            if (keep) {
+                atomicOr(rank_bits + (pos >> 5), 1u << (pos & 31u));
+                if (nf > 1) atomicAdd(&fr[f].kept, 1u);
+            }
         }
         const uint32_t mask = __ballot_sync(0xffffffffu, keep);
         if (!mask) continue;
@@ -950,54 +965,122 @@ __global__ void __launch_bounds__(256)
         if (lane == leader) slot = atomicAdd(&plan->kept.n, (uint32_t)__popc(mask));
         slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(mask & lanemask_lt());
         if (keep) {
-            kept_key[slot] = cmin[a];
+            kept_key[slot] = pos;
             kept_val[slot] = a;
         }
     }
 }
 
-// a6: rank of each kept root in smallest-index order.
-// With several frames, kept components are in frame order (their smallest
-// rows are), and each frame numbers its own from 0: rank - the kept
-// components of the frames before it (an exclusive scan every block makes of
-// the frames' kept counts, kMaxFramesPerCall at most).
-__global__ void __launch_bounds__(256)
-    k_rank(Plan *plan, const uint32_t *__restrict__ ka, const uint32_t *__restrict__ kb,
-           const uint32_t *__restrict__ va, const uint32_t *__restrict__ vb, const Frame *__restrict__ fr,
-           uint32_t nf, int32_t *__restrict__ crank)
+// k_rankscan: rank_prefix[w] = set bits in words 0..w-1 of the bitmap (one
+// pass, decoupled look-back over tiles of kRankTileWords words; waits
+// bounded by prm.wait_cap like the sort's).
+constexpr int kRankThreads = 256;
+constexpr int kRankWordsPerThread = 8;
+constexpr uint32_t kRankTileWords = kRankThreads * kRankWordsPerThread;
+__global__ void __launch_bounds__(kRankThreads)
+    k_rankscan(Plan *plan, Params prm, const uint32_t *__restrict__ rank_bits,
+               uint32_t *__restrict__ rank_prefix, unsigned long long *__restrict__ tstat)
 {
-    __shared__ uint32_t s_base[kMaxFramesPerCall];
-    __shared__ uint32_t s_tot[8];
+    __shared__ uint32_t s_tile, s_warp[kRankThreads / 32];
+    __shared__ unsigned long long s_prefix;
     if (block_aborted(&plan->status)) return;
-    const uint32_t k = plan->kept.n;
-    const bool in_b = (plan->kept.npasses & 1u) != 0;
-    const uint32_t *__restrict__ v = in_b ? vb : va;
-    const uint32_t *__restrict__ key = in_b ? kb : ka;
-    if (nf > 1) {
-        // exclusive scan of fr[*].kept in chunks of 256 (8 warps)
-        const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-        uint32_t carry = 0;
-        for (uint32_t c0 = 0; c0 < nf; c0 += 256) {
-            const uint32_t f = c0 + t;
-            const uint32_t x = f < nf ? fr[f].kept : 0u;
-            uint32_t incl = x;
+    constexpr unsigned long long kAgg = 1ull << 62, kIncl = 2ull << 62, kMask = (1ull << 62) - 1;
+    const uint32_t nwords = (plan->sort.n + 31) / 32;
+    const uint32_t ntiles = (nwords + kRankTileWords - 1) / kRankTileWords;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&plan->rank_tile_counter, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t w0 = tile * kRankTileWords + tid * kRankWordsPerThread;
+        uint32_t c[kRankWordsPerThread], run = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            if (lane == 31) s_tot[w] = incl;
-            __syncthreads();
-            uint32_t before = carry;
-            for (int j = 0; j < w; ++j) before += s_tot[j];
-            if (f < nf) s_base[f] = before + incl - x;
-            for (int j = 0; j < 8; ++j) carry += s_tot[j];
-            __syncthreads();
+        for (int i = 0; i < kRankWordsPerThread; ++i) {
+            c[i] = w0 + i < nwords ? (uint32_t)__popc(rank_bits[w0 + i]) : 0u;
+            run += c[i];
         }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < kRankThreads / 32; ++w) tot += s_warp[w];
+            __syncwarp();
+            if (lane == 0) {
+                uint32_t acc = 0;
+                for (int w = 0; w < kRankThreads / 32; ++w) {
+                    const uint32_t v = s_warp[w];
+                    s_warp[w] = acc;
+                    acc += v;
+                }
+                st_relaxed64(tstat + tile, (tile == 0 ? kIncl : kAgg) | tot);
+            }
+            unsigned long long prefix = 0;
+            if (tile > 0) {  // look-back, one preceding tile per lane per step
+                int64_t p = (int64_t)tile - 1;
+                uint32_t it = 0;
+                for (;;) {
+                    const int64_t q = p - lane;
+                    unsigned long long sv = q >= 0 ? ld_relaxed64(tstat + q) : kIncl;
+                    while (!__all_sync(0xffffffffu, (sv & ~kMask) != 0)) {
+                        if (++it > prm.wait_cap) {
+                            if (lane == 0) atomicOr(&plan->status, ST_WAIT_TIMEOUT);
+                            break;
+                        }
+                        spin_pause(it);
+                        if ((sv & ~kMask) == 0) sv = ld_relaxed64(tstat + q);
+                    }
+                    const uint32_t incl_m = __ballot_sync(0xffffffffu, (sv & ~kMask) == kIncl);
+                    const int stop = incl_m ? __ffs(incl_m) - 1 : 31;
+                    unsigned long long part = (lane <= stop && q >= 0) ? (sv & kMask) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    prefix += part;
+                    if (incl_m || it > prm.wait_cap) break;
+                    p -= 32;
+                }
+                if (lane == 0) st_relaxed64(tstat + tile, kIncl | ((prefix + tot) & kMask));
+            }
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        uint32_t before = (uint32_t)s_prefix + s_warp[warp] + (incl - run);
+#pragma unroll
+        for (int i = 0; i < kRankWordsPerThread; ++i) {
+            if (w0 + i < nwords) rank_prefix[w0 + i] = before;
+            before += c[i];
+        }
+        __syncthreads();
     }
+}
+
+// Set bits of the bitmap before position p.
+__device__ __forceinline__ uint32_t bits_before(const uint32_t *__restrict__ bits,
+                                                const uint32_t *__restrict__ prefix, uint32_t p)
+{
+    const uint32_t w = p >> 5, b = p & 31u;
+    return prefix[w] + (uint32_t)__popc(bits[w] & ((1u << b) - 1u));
+}
+
+// k_rank: every kept root's number within its frame.
+__global__ void __launch_bounds__(256)
+    k_rank(Plan *plan, const uint32_t *__restrict__ kept_key, const uint32_t *__restrict__ kept_val,
+           const uint32_t *__restrict__ rank_bits, const uint32_t *__restrict__ rank_prefix,
+           const Frame *__restrict__ fr, uint32_t nf, int32_t *__restrict__ crank)
+{
+    if (call_aborted(&plan->status)) return;
+    const uint32_t k = plan->kept.n;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
-        const uint32_t base = nf > 1 ? s_base[frame_of_row(fr, nf, key[t])] : 0u;
-        crank[v[t]] = (int32_t)(t - base);
+        const uint32_t pos = kept_key[t];
+        uint32_t r = bits_before(rank_bits, rank_prefix, pos);
+        if (nf > 1) r -= bits_before(rank_bits, rank_prefix, fr[frame_of_pos(fr, nf, pos)].pos_off);
+        crank[kept_val[t]] = (int32_t)r;
     }
 }
 
@@ -1126,7 +1209,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, cudaStream_t st)
                                                  ws.cmin, prm.union_cap);
     FEC_MARK(ws, "k_flatten_stats", st);
     k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, ws.frames, prm.nf,
-                                  ws.kept_key_a(), ws.kept_val_a());
+                                  ws.kept_key_a(), ws.kept_val_a(), ws.rank_bits);
     FEC_MARK(ws, "k_kept", st);
     return cudaGetLastError();
 }
@@ -1135,8 +1218,12 @@ cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bo
                            cudaStream_t st)
 {
     const int grid1 = grid_for(ws, prm.n, 256, 8);
-    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_key_a(), ws.kept_key_b(),
-                                                        ws.kept_val_a(), ws.kept_val_b(), ws.frames,
+    const uint64_t words = ((uint64_t)prm.n + 31) / 32;
+    k_rankscan<<<grid_for(ws, words, kRankTileWords, 4), kRankThreads, 0, st>>>(
+        ws.plan, prm, ws.rank_bits, ws.rank_prefix, ws.rank_status);
+    FEC_MARK(ws, "k_rankscan", st);
+    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_key_a(), ws.kept_val_a(),
+                                                        ws.rank_bits, ws.rank_prefix, ws.frames,
                                                         prm.nf, ws.crank);
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
