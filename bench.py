@@ -39,20 +39,21 @@ FALLBACK_HBM_GBS = 6800.0
 # (n = points, Ms = sub-cells, Mc = cells); compulsory traffic only (each
 # array the kernel must read or write, once):
 #   k_bbox           xyz 12
-#   k_keys           xyz 12 + key 4 + payload 8
+#   k_keys           xyz 12 (packed layout: it only makes the digit histograms;
+#                    the sort's first pass computes keys and payloads itself)
 #   sort pass        (key 4 + payload 8) read and written
 #   k_cells          key + payload 12, record 16 + sub-cell of position 4 per point;
 #                    start 4 + code 1 per sub-cell; key 8 + first sub-cell 4 per cell
 #   k_subcell_stats  record 16 per point; start 4, box 32, smallest index 4,
-#                    representative 16, parent/size/min/rank 16 per sub-cell
+#                    representative 4, parent/size/min/rank 16 per sub-cell
 #   k_region         range 4, neighbour record 32, neighbour first sub-cells 52 per
-#                    cell; box 32, representative 16, parent 4 per sub-cell
+#                    cell; box 32, representative 4, parent 4 per sub-cell
 #   k_flatten_stats  parent 4+4, count 4, smallest index 4, size/min 8 per sub-cell
 #   k_labels         payload 8, sub-cell of position 4, label 4 per point;
 #                    sub-cell label 4 per sub-cell
 KERNEL_BYTES = {
     "k_bbox": lambda n, Ms, Mc: 12 * n,
-    "k_keys": lambda n, Ms, Mc: 12 * n,   # packed layout: histograms only, the sort's first pass makes the keys
+    "k_keys": lambda n, Ms, Mc: 12 * n,
     "onesweep_u32": lambda n, Ms, Mc: 24 * n,
     "k_cells": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
     "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 60 * Ms,
@@ -221,6 +222,41 @@ def time_oracle(cloud, target_points):
     return sample.n / dt / 1e6, desc, sample.n, dt
 
 
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def time_oracle_batch(frames, processes=None):
+    """Config 4's all-core oracle baseline: one oracle call per frame across
+    the host's cores (a spawn process pool); frames per second and the
+    cores used."""
+    import oracle
+
+    procs = processes or os.cpu_count() or 1
+    jobs = [(f.xyz, f.d, f.min_size, f.max_size) for f in frames]
+    oracle.cluster_many(jobs[:procs], processes=procs)  # pool start-up and compile, untimed
+    t0 = time.perf_counter()
+    oracle.cluster_many(jobs, processes=procs)
+    dt = time.perf_counter() - t0
+    return {"frames_per_s": len(frames) / dt, "Mpoints_per_s": sum(f.n for f in frames) / dt / 1e6,
+            "seconds": round(dt, 2), "cores": procs, "kind": "oracle", **host_info(),
+            "sample": f"all {len(frames)} frames of the batch, one oracle call per frame"}
+
+
 def dist_setup(backend):
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
@@ -274,14 +310,15 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "n": cloud.n, "d": cloud.d, "min_size": cloud.min_size,
                    "max_size": cloud.max_size, "sample": desc, "parallelism": "1 host core"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                         **host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def measure_batch(fec, torch, dev, stream, steps, seed=4):
+def measure_batch(fec, torch, dev, stream, steps, seed=4, oracle_baseline=True):
     """Batched frames/s on the 256-frame workload: one fec_cluster_batch call
     per step (graph-captured, autotuned lanes), against the plain path of one
     fec_cluster call per frame.  Device-resident inputs."""
@@ -322,10 +359,13 @@ def measure_batch(fec, torch, dev, stream, steps, seed=4):
         ms_plain = e0.elapsed_time(e1)
         same = bool(torch.equal(batch_lab, lab))
     nf = len(frames)
-    return {"frames": nf, "points": int(offs[-1]), "frames_per_s": nf / (ms_batch * 1e-3),
-            "ms_per_batch": ms_batch, "Mpoints_per_s": offs[-1] / (ms_batch * 1e-3) / 1e6,
-            "plain_frames_per_s": nf / (ms_plain * 1e-3), "plain_ms": ms_plain,
-            "labels_equal_plain": same}
+    out = {"frames": nf, "points": int(offs[-1]), "frames_per_s": nf / (ms_batch * 1e-3),
+           "ms_per_batch": ms_batch, "Mpoints_per_s": offs[-1] / (ms_batch * 1e-3) / 1e6,
+           "plain_frames_per_s": nf / (ms_plain * 1e-3), "plain_ms": ms_plain,
+           "labels_equal_plain": same}
+    if oracle_baseline:
+        out["cpu_baseline_all_cores"] = time_oracle_batch(frames)
+    return out
 
 
 def measure_frame(fec, torch, dev, stream, steps=20):
@@ -599,7 +639,8 @@ def run_ours(args):
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extra["frame_120k"] = measure_frame(fec, torch, dev, stream)
-        extra["batch_256"] = measure_batch(fec, torch, dev, stream, max(3, args.steps))
+        extra["batch_256"] = measure_batch(fec, torch, dev, stream, max(3, args.steps),
+                                           oracle_baseline=not args.no_cpu_baseline)
         extra["voxel_sweep"] = measure_voxel_sweep(fec, torch, dev, stream)
         extra["serve"] = measure_serve(fec, duration=args.serve_seconds, warmup=args.serve_warmup)
         extra["serve_heavy"] = measure_serve(fec, duration=max(1.0, args.serve_seconds / 2),
@@ -609,7 +650,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, sn, dt = time_oracle(cloud, args.cpu_points)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(dt, 2)}
+               "seconds": round(dt, 2), **host_info()}
 
     if rank == 0:
         line = {
@@ -654,9 +695,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="map_27m")
-    ap.add_argument("--cpu-points", type=int, default=4_000_000,
-                    help="oracle sample size for cpu_baseline (about 10-30 s of CPU work)")
-    ap.add_argument("--ref-points", type=int, default=1_000_000,
+    ap.add_argument("--cpu-points", type=int, default=2_000_000,
+                    help="oracle sample size for cpu_baseline (the same crop as --impl reference)")
+    ap.add_argument("--ref-points", type=int, default=2_000_000,
                     help="oracle sample size per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

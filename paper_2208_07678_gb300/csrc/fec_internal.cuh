@@ -508,7 +508,10 @@ inline int grid_for(const Workspace &ws, uint64_t items, uint64_t per_block, int
 
 // Regions have kRegionCellsPerBlock cells, fewer (down to kRegionMinCells)
 // when the cloud has too few cells to give every block of the grid two.
-constexpr uint32_t kRegionMinCells = 64;
+#ifndef FEC_REGION_MIN_CELLS
+#define FEC_REGION_MIN_CELLS 32
+#endif
+constexpr uint32_t kRegionMinCells = FEC_REGION_MIN_CELLS;
 
 // Blocks of the region kernel for n points (kRegionBlocksPerSM per SM, at most
 // one per possible region of the smallest size).

@@ -111,3 +111,14 @@ def test_oracle_sample_is_a_bounded_density_preserving_crop(bench):
 def test_unknown_workload_is_refused(bench):
     with pytest.raises(SystemExit):
         bench.make_workload("no_such_workload")
+
+
+def test_host_info_and_all_core_batch_baseline():
+    import bench
+    from paper_2208_07678_gb300 import synth
+
+    info = bench.host_info()
+    assert info["nproc"] >= 1 and isinstance(info["cpu_model"], str) and info["cpu_model"]
+    frames = synth.batch_256(seed=8, n_frames=3, lo=500, hi=1_000)
+    out = bench.time_oracle_batch(frames, processes=2)
+    assert out["frames_per_s"] > 0 and out["cores"] == 2 and out["kind"] == "oracle"
