@@ -132,10 +132,10 @@ __device__ __forceinline__ void block_box(int32_t lo[3], int32_t hi[3], int32_t 
 }
 
 // Work units of the bounding-box and key kernels: each sort tile (which never
-// straddles two frames) split into kUnitsPerTile chunks.  Unit u covers
+// straddles two frames) split into kUnitsPerTile chunks of about 1,024 points.  Unit u covers
 // frame-local indices [first, first + count) of frame f (count may be 0).
-constexpr uint32_t kUnitsPerTile = 5;
-constexpr uint32_t kUnit = kSortTile / kUnitsPerTile;  // 1024 points
+constexpr uint32_t kUnitsPerTile = kSortTile >= 2048 ? kSortTile / 1024 : 1;
+constexpr uint32_t kUnit = kSortTile / kUnitsPerTile;  // about 1024 points
 static_assert(kUnit * kUnitsPerTile == kSortTile, "units split a tile evenly");
 struct TileSpan {
     uint32_t f, first, count;

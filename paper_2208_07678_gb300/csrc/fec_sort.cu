@@ -25,7 +25,10 @@ static_assert(kSortThreads >= kRadixBins, "the digit loops need one thread per d
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr int kLookWin = 8;  // preceding tiles read per look-back step
+#ifndef FEC_SORT_LOOKWIN
+#define FEC_SORT_LOOKWIN 8
+#endif
+constexpr int kLookWin = FEC_SORT_LOOKWIN;  // preceding tiles read per look-back step
 
 template <typename KeyT, typename ValT>
 struct SortSmem {
