@@ -58,18 +58,18 @@ constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;            // 64-bit keys
 #ifndef FEC_SORT_THREADS
-#define FEC_SORT_THREADS 512
+#define FEC_SORT_THREADS 256
 #endif
 #ifndef FEC_SORT_IPT
 #define FEC_SORT_IPT 10
 #endif
 #ifndef FEC_SORT_MINB
-#define FEC_SORT_MINB 2
+#define FEC_SORT_MINB 4
 #endif
 constexpr int kSortThreads = FEC_SORT_THREADS;
 constexpr int kSortIPT = FEC_SORT_IPT;   // items per thread
 constexpr int kSortMinBlocks = FEC_SORT_MINB;
-constexpr int kSortTile = kSortThreads * kSortIPT;   // 5120 keys per tile
+constexpr int kSortTile = kSortThreads * kSortIPT;   // 2560 keys per tile
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 8;
 constexpr int kScanTile = kScanThreads * kScanIPT;   // 2048 positions per tile

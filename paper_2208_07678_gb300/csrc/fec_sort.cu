@@ -26,7 +26,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 #ifndef FEC_SORT_LOOKWIN
-#define FEC_SORT_LOOKWIN 8
+#define FEC_SORT_LOOKWIN 4
 #endif
 constexpr int kLookWin = FEC_SORT_LOOKWIN;  // preceding tiles read per look-back step
 

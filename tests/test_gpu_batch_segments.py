@@ -5,8 +5,8 @@ at the seams of that design; each frame's labels must equal the oracle on the
 frame alone (exact, tolerance 0):
 
 * frames of 1 to 9 points next to each other (several frame starts inside
-  one thread's positions of the cell-table scan), and frames of exactly one
-  sort tile (5,120 points) and one more;
+  one thread's positions of the cell-table scan), and frames of one and two
+  sort tiles (2,560 and 5,120 points) and one more or less;
 * identical frames (the same coordinates in every frame: cells of different
   frames coincide in space and must never join);
 * more frames than one block of the planning kernel handles at once (300),
@@ -78,7 +78,7 @@ def test_tiny_frames_side_by_side(ctx):
 
 def test_frames_at_sort_tile_sizes(ctx):
     rng = np.random.default_rng(102)
-    sizes = [5120, 5121, 5119, 10240, 1, 5120]
+    sizes = [2560, 2561, 2559, 5120, 5121, 5119, 10240, 1, 2560]
     frames = [_blob(rng, n, 3.0) for n in sizes]
     _check(ctx, frames, [0.25] * len(frames))
 
