@@ -209,6 +209,7 @@ struct Summary {
 
 __global__ void k_summary(const Plan *plan, Summary *out)
 {
+    grid_enter();
     if (threadIdx.x == 0) {
         out->status = plan->status;
         out->k = plan->kept.n;
@@ -594,7 +595,7 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
             return FEC_ERR_CUDA;
         FEC_MARK(ws, "d2h_labels", ctx->stream);
     }
-    k_summary<<<1, 32, 0, ctx->stream>>>(ws.plan, ctx->summary_dev);
+    launch(k_summary, 1, 32, 0, ctx->stream, ws.plan, ctx->summary_dev);
     if (cudaMemcpyAsync(ctx->summary_host, ctx->summary_dev, sizeof(Summary),
                         cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         return FEC_ERR_CUDA;

@@ -58,6 +58,7 @@ struct FrameResult {
 __global__ void k_group_result(const Plan *plan, const Frame *fr, uint32_t nf,
                                const int32_t *__restrict__ batch_index, FrameResult *out)
 {
+    grid_enter();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         FrameResult r;
         r.status = plan->status;
@@ -449,7 +450,7 @@ fec_status capture(BatchEngine &e, const Config &c, const std::vector<Group> &gr
             fa.single = false;
             err = enqueue_cluster(ln.ws, xyz, prm, fa, labels, false, ln.st);
             if (err == cudaSuccess) {
-                k_group_result<<<(nf + 255) / 256, 256, 0, ln.st>>>(ln.ws.plan, ln.ws.frames, nf,
+                launch(k_group_result, (nf + 255) / 256, 256, 0, ln.st, ln.ws.plan, ln.ws.frames, nf,
                                                                      g.index_dev + first[gi], e.res_dev);
                 err = cudaGetLastError();
             }

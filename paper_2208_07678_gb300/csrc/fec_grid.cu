@@ -42,6 +42,7 @@ __device__ __forceinline__ T warp_max(T v)
 __global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint32_t n,
                        uint32_t wait_cap, int single, long long min_size, long long max_size)
 {
+    grid_enter();
     const int t = threadIdx.x;
     if (blockIdx.x == 0) {
         if (t < 3) {
@@ -192,6 +193,7 @@ template <bool MULTI>
 __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, Plan *plan,
                                               Frame *__restrict__ fr, Params prm)
 {
+    grid_enter();
     __shared__ int32_t s_lo[3][8], s_hi[3][8];
     __shared__ uint32_t s_st;
     int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX};
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, Pla
 // index; disable the rest of the pipeline on a data error.  One block.
 __global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr, Params prm)
 {
+    grid_enter();
     __shared__ uint32_t s_cm[3];
     __shared__ uint32_t s_scan[256];
     __shared__ int s_perm0;
@@ -484,6 +487,7 @@ __global__ void __launch_bounds__(256)
     k_keys(const float *__restrict__ xyz, Plan *plan, Params prm, const Frame *__restrict__ fr,
            uint32_t *__restrict__ fhist, void *__restrict__ keys, Clears clr)
 {
+    grid_enter();
     __shared__ uint32_t h[kMaxPasses][kRadixBins];
     if (plan->sort.key64)
         keys_body<unsigned long long, STORE, MULTI>(xyz, plan, prm, fr, fhist, (unsigned long long *)keys,
@@ -757,6 +761,7 @@ __global__ void __launch_bounds__(kScanThreads, MULTI ? 3 : 4)  // the frame wal
             uint32_t *__restrict__ cframe, const Frame *__restrict__ fr,
             unsigned long long *__restrict__ tstat)
 {
+    grid_enter();
     __shared__ CellsSmem C;
     using u64 = unsigned long long;
     if (plan->sort.key64)
@@ -817,6 +822,7 @@ __global__ void __launch_bounds__(256)
                     int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps,
                     const Frame *__restrict__ fr)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     const int32_t lo0[3] = {fr[0].lo[0], fr[0].lo[1], fr[0].lo[2]};  // one frame: its origin
@@ -1019,6 +1025,7 @@ __global__ void __launch_bounds__(256)
                     SubBox *__restrict__ box, uint32_t *__restrict__ sminidx, uint32_t *__restrict__ reps,
                     const Frame *__restrict__ fr, uint32_t huge_blocks)
 {
+    grid_enter();
     if (blockIdx.x < huge_blocks)
         subcell_huge(plan, prm, rec, sc_start, big, box, sminidx, reps, fr, blockIdx.x, huge_blocks);
     else
@@ -1037,6 +1044,7 @@ __global__ void __launch_bounds__(256)
             uint8_t *__restrict__ cocc, const uint32_t *__restrict__ cframe,
             const Frame *__restrict__ fr, uint32_t nf)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
     const uint32_t b2 = plan->bits[2];
@@ -1078,14 +1086,14 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, co
                            : grid_for(ws, prm.n, 1024, 8);
     const uint64_t hist_words = (uint64_t)prm.nf * kMaxPasses * kRadixBins;
     const int igrid = (int)std::min<uint64_t>((hist_words + 2047) / 2048, (uint64_t)ws.sms * 4);
-    k_init<<<igrid < 1 ? 1 : igrid, 256, 0, st>>>(ws.plan, ws.frames, prm.nf, ws.fhist, prm.n,
+    launch(k_init, igrid < 1 ? 1 : igrid, 256, 0, st, ws.plan, ws.frames, prm.nf, ws.fhist, prm.n,
                                                   prm.wait_cap, fa.single ? 1 : 0, fa.min_size,
                                                   fa.max_size);
     FEC_MARK(ws, "k_init", st);
-    if (multi) k_bbox<true><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
-    else k_bbox<false><<<grid, 256, 0, st>>>(xyz, ws.plan, ws.frames, prm);
+    if (multi) launch(k_bbox<true>, grid, 256, 0, st, xyz, ws.plan, ws.frames, prm);
+    else launch(k_bbox<false>, grid, 256, 0, st, xyz, ws.plan, ws.frames, prm);
     FEC_MARK(ws, "k_bbox", st);
-    k_plan<<<1, 256, 0, st>>>(ws.plan, ws.frames, prm);
+    launch(k_plan, 1, 256, 0, st, ws.plan, ws.frames, prm);
     FEC_MARK(ws, "k_plan", st);
     Clears clr;
     clr.sort_status = ws.sort_status;
@@ -1104,13 +1112,13 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, co
     clr.max_words = std::max({clr.sort_words, clr.scan_words, clr.slab_words, clr.rank_words});
     // packed layout: the sort's first pass computes the keys itself
     if (prm.packed && !multi)
-        k_keys<false, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+        launch(k_keys<false, false>, grid, 256, 0, st, xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     else if (prm.packed)
-        k_keys<false, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+        launch(k_keys<false, true>, grid, 256, 0, st, xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     else if (!multi)
-        k_keys<true, false><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+        launch(k_keys<true, false>, grid, 256, 0, st, xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     else
-        k_keys<true, true><<<grid, 256, 0, st>>>(xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
+        launch(k_keys<true, true>, grid, 256, 0, st, xyz, ws.plan, prm, ws.frames, ws.fhist, ws.keys_a, clr);
     FEC_MARK(ws, "k_keys", st);
     return cudaGetLastError();
 }
@@ -1129,26 +1137,26 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
     ws.plan, prm, ws.keys_a, va, ws.keys_b, vb, xyz, ws.rec, ws.sc_of, ws.sc_start, ws.scode,     \
         ws.cell_key, ws.cell_sc, ws.cframe, ws.frames, ws.scan_status
     if (prm.packed && prm.nf == 1)
-        k_cells<u64, false><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va64, vb64));
+        launch(k_cells<u64, false>, grid, kScanThreads, 0, st, FEC_CELLS_ARGS(va64, vb64));
     else if (prm.packed)
-        k_cells<u64, true><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va64, vb64));
+        launch(k_cells<u64, true>, grid, kScanThreads, 0, st, FEC_CELLS_ARGS(va64, vb64));
     else if (prm.nf == 1)
-        k_cells<u32, false><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va32, vb32));
+        launch(k_cells<u32, false>, grid, kScanThreads, 0, st, FEC_CELLS_ARGS(va32, vb32));
     else
-        k_cells<u32, true><<<grid, kScanThreads, 0, st>>>(FEC_CELLS_ARGS(va32, vb32));
+        launch(k_cells<u32, true>, grid, kScanThreads, 0, st, FEC_CELLS_ARGS(va32, vb32));
 #undef FEC_CELLS_ARGS
     FEC_MARK(ws, "k_cells", st);
-    k_subcell_stats<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
+    launch(k_subcell_stats, grid1, 256, 0, st, ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
                                            ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps,
                                            ws.frames);
     FEC_MARK(ws, "k_subcell_stats", st);
     const int huge_blocks = grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2);
     const int big_blocks = grid_for(ws, prm.n / (prm.big_subcell + 1), 8, 4);
-    k_subcell_large<<<huge_blocks + big_blocks, 256, 0, st>>>(ws.plan, prm, ws.rec, ws.sc_start, ws.big,
+    launch(k_subcell_large, huge_blocks + big_blocks, 256, 0, st, ws.plan, prm, ws.rec, ws.sc_start, ws.big,
                                                              ws.box, ws.sminidx, ws.reps, ws.frames,
                                                              (uint32_t)huge_blocks);
     FEC_MARK(ws, "k_subcell_large", st);
-    k_slabs<<<grid1, 256, 0, st>>>(ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
+    launch(k_slabs, grid1, 256, 0, st, ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
                                   ws.col_lo, ws.col_hi, ws.cocc, ws.cframe, ws.frames, prm.nf);
     FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();

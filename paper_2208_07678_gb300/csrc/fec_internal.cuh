@@ -21,6 +21,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -53,6 +54,12 @@ enum {
     CTR_QUEUED = 5,       // pairs queued for the warp-per-pair kernel
     CTR_EDGES = 6,        // edges between regions joined after the region step
 };
+
+// Kernels are launched with programmatic stream serialisation (grid_enter(),
+// launch()); 0 gives plain stream order.
+#ifndef FEC_PDL
+#define FEC_PDL 1
+#endif
 
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
@@ -423,6 +430,24 @@ __device__ __forceinline__ bool block_aborted(const uint32_t *status)
     return __syncthreads_or(threadIdx.x == 0 && call_aborted(status)) != 0;
 }
 
+// Programmatic dependent launch.  Kernels are launched (launch() below) so
+// that the launch of a kernel is prepared while the previous kernel of the
+// stream is still running, and its blocks start as that kernel's blocks
+// exit, without the gap of a plain stream dependency.  Every kernel calls
+// grid_enter() before its first access to global memory: it waits until the
+// previous kernel has finished and its writes are visible (so ordering stays
+// transitive along the stream: each kernel finishes only after its
+// predecessor has).  No kernel signals its dependents early: resident blocks
+// of the next kernel waiting beside a running one measured slower (map, batch)
+// than dependents released as blocks exit.  Outside such a launch the wait
+// returns at once.
+__device__ __forceinline__ void grid_enter()
+{
+#if FEC_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers (one stream; all asynchronous)
 // ---------------------------------------------------------------------------
@@ -496,6 +521,27 @@ struct Workspace {
 // (no-op unless tracing is enabled).
 void trace_mark(const Workspace &ws, const char *name, cudaStream_t st);
 #define FEC_MARK(ws, name, st) trace_mark((ws), (name), (st))
+
+// Enqueue kernel k on st with `grid` blocks of `block` threads and `smem`
+// bytes of dynamic shared memory, allowed to be scheduled before the
+// previous kernel of st has finished (the kernel's grid_enter() waits for
+// it).  Launch errors are left for the caller's cudaGetLastError().
+template <typename... P, typename... A>
+inline void launch(void (*k)(P...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t st,
+                   A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = FEC_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // Blocks of a grid-stride kernel over `items` work items, `per_block` per
 // block and step: as many as the items need, at most `per_sm` per SM.

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
                const Plan *__restrict__ plan, Params prm, const Frame *__restrict__ fr,
                const uint32_t *__restrict__ fhist)
 {
+    grid_enter();
     // Two look-back status arrays alternate between passes: this pass reads
     // and publishes in `tstat`, and clears its own tiles' slots in the other
     // array for the next pass (which starts only after this one finishes).
@@ -329,11 +330,11 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
         if constexpr (kXyz) {
             if (p == 0 && src.xyz) {
                 if (seg)
-                    k_onesweep<KeyT, ValT, true, true><<<grid, kSortThreads, smem, st>>>(
+                    launch(k_onesweep<KeyT, ValT, true, true>, grid, kSortThreads, smem, st,
                         ctl, nullptr, nullptr, kout, vout, tile_status, tstride, p, status, src.xyz,
                         src.plan, src.prm, src.frames, src.fhist);
                 else
-                    k_onesweep<KeyT, ValT, true, false><<<grid, kSortThreads, smem, st>>>(
+                    launch(k_onesweep<KeyT, ValT, true, false>, grid, kSortThreads, smem, st,
                         ctl, nullptr, nullptr, kout, vout, tile_status, tstride, p, status, src.xyz,
                         src.plan, src.prm, src.frames, src.fhist);
                 done = true;
@@ -341,11 +342,11 @@ cudaError_t launch_sort_t(const Workspace &ws, const char *name, SortCtl *ctl, v
         }
         const ValT *vsrc = (p == 0 && identity_vals) ? nullptr : vin;
         if (!done && seg)
-            k_onesweep<KeyT, ValT, false, true><<<grid, kSortThreads, smem, st>>>(
+            launch(k_onesweep<KeyT, ValT, false, true>, grid, kSortThreads, smem, st,
                 ctl, kin, vsrc, kout, vout, tile_status, tstride, p, status, nullptr, nullptr,
                 src.prm, src.frames, src.fhist);
         else if (!done)
-            k_onesweep<KeyT, ValT, false, false><<<grid, kSortThreads, smem, st>>>(
+            launch(k_onesweep<KeyT, ValT, false, false>, grid, kSortThreads, smem, st,
                 ctl, kin, vsrc, kout, vout, tile_status, tstride, p, status, nullptr, nullptr,
                 src.prm, src.frames, src.fhist);
         e = cudaGetLastError();

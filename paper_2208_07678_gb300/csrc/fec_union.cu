@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(256, 4)
            unsigned long long *__restrict__ edge_set, uint32_t edge_set_size,
            const uint32_t *__restrict__ cframe, const Frame *__restrict__ fr)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     // the boundary-edge hash set of k_edges starts empty
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < edge_set_size;
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
              uint2 *__restrict__ pairq, uint32_t qcap, uint2 *__restrict__ edges, uint32_t ecap,
              uint32_t *__restrict__ scratch, uint32_t scap)
 {
+    grid_enter();
     extern __shared__ __align__(16) unsigned char region_smem[];
     RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
     if (block_aborted(&plan->status)) return;
@@ -765,6 +767,7 @@ __global__ void __launch_bounds__(256)
     k_edges(Plan *plan, const uint2 *__restrict__ edges, uint32_t ecap, uint32_t *parent,
             unsigned long long *__restrict__ set, uint32_t set_mask, uint32_t union_cap)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t ne = min(plan->edges_n, ecap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
@@ -800,6 +803,7 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
     k_pairs(Plan *plan, Params prm, const SubBox *__restrict__ box, const Rec *__restrict__ rec,
             uint32_t *parent, const uint2 *__restrict__ pairq, uint32_t qcap)
 {
+    grid_enter();
     if (block_aborted(&plan->status)) return;
     const uint32_t nq = min(plan->pairq_n, qcap);
     const int lane = threadIdx.x & 31;
@@ -849,6 +853,7 @@ __global__ void __launch_bounds__(256, 4)
                     uint32_t *parent, uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
                     uint32_t union_cap)
 {
+    grid_enter();
     if (block_aborted(&plan->status)) return;
     // Each block takes one contiguous range of sub-cells (a compact piece of
     // space, so few distinct components) and sums sizes and smallest indices
@@ -938,6 +943,7 @@ __global__ void __launch_bounds__(256)
            uint32_t *__restrict__ kept_key, uint32_t *__restrict__ kept_val,
            uint32_t *__restrict__ rank_bits)
 {
+    grid_enter();
     if (block_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     const int lane = threadIdx.x & 31;
@@ -981,6 +987,7 @@ __global__ void __launch_bounds__(kRankThreads)
     k_rankscan(Plan *plan, Params prm, const uint32_t *__restrict__ rank_bits,
                uint32_t *__restrict__ rank_prefix, unsigned long long *__restrict__ tstat)
 {
+    grid_enter();
     __shared__ uint32_t s_tile, s_warp[kRankThreads / 32];
     __shared__ unsigned long long s_prefix;
     if (block_aborted(&plan->status)) return;
@@ -1074,6 +1081,7 @@ __global__ void __launch_bounds__(256)
            const uint32_t *__restrict__ rank_bits, const uint32_t *__restrict__ rank_prefix,
            const Frame *__restrict__ fr, uint32_t nf, int32_t *__restrict__ crank)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t k = plan->kept.n;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
@@ -1091,6 +1099,7 @@ __global__ void __launch_bounds__(256)
     k_sclabel(Plan *plan, const uint32_t *__restrict__ parent, const int32_t *__restrict__ crank,
               int32_t *__restrict__ sclab, int32_t *__restrict__ labels, uint32_t n)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x)
@@ -1112,6 +1121,7 @@ __global__ void __launch_bounds__(256)
              uint32_t idx_stride, const uint32_t *__restrict__ sc_of,
              const int32_t *__restrict__ sclab, int32_t *__restrict__ labels, uint32_t rows)
 {
+    grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t n = plan->sort.n;
     const uint32_t *__restrict__ idx = (plan->sort.npasses & 1u) ? idx_b : idx_a;
@@ -1180,35 +1190,35 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, cudaStream_t st)
         ctx_setup_done(attr_ctx);
     }
     const int grid1 = grid_for(ws, prm.n, 256, 8);  // one item (cell, sub-cell, edge) per thread
-    k_nbrs<<<grid1, 256, 0, st>>>(ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
+    launch(k_nbrs, grid1, 256, 0, st, ws.plan, prm, ws.cell_key, ws.cell_sc, ws.slab_lo, ws.slab_hi,
                                         ws.col_lo, ws.col_hi, ws.cocc, ws.nb_first, ws.nb_cnt,
                                         ws.edge_set, (uint32_t)ws.edge_set_size, ws.cframe, ws.frames);
     FEC_MARK(ws, "k_nbrs", st);
     const uint32_t rgrid = region_grid(ws, prm.n);
     const uint32_t scap = region_scratch(ws, ws.cap_n);
     if (!wide)
-        k_region<false><<<rgrid, kRegionThreads, smem, st>>>(
+        launch(k_region<false>, rgrid, kRegionThreads, smem, st,
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     else
-        k_region<true><<<rgrid, kRegionThreads, smem, st>>>(
+        launch(k_region<true>, rgrid, kRegionThreads, smem, st,
             ws.plan, prm, ws.cell_key, ws.cell_sc, ws.box, ws.reps, ws.rec, ws.parent, ws.nb_first,
             ws.nb_cnt, ws.pairq, qcap, ws.edges, ecap, ws.scratch, scap);
     FEC_MARK(ws, "k_region", st);
-    k_edges<<<grid1, 256, 0, st>>>(ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
+    launch(k_edges, grid1, 256, 0, st, ws.plan, ws.edges, ecap, ws.parent, ws.edge_set,
                                         (uint32_t)(ws.edge_set_size - 1), prm.union_cap);
     FEC_MARK(ws, "k_edges", st);
     if (!wide)
-        k_pairs<false><<<grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
+        launch(k_pairs<false>, grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st, ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                              ws.pairq, qcap);
     else
-        k_pairs<true><<<grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st>>>(ws.plan, prm, ws.box, ws.rec, ws.parent,
+        launch(k_pairs<true>, grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st, ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                             ws.pairq, qcap);
     FEC_MARK(ws, "k_pairs", st);
-    k_flatten_stats<<<grid1, 256, 0, st>>>(ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
+    launch(k_flatten_stats, grid1, 256, 0, st, ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
                                                  ws.cmin, prm.union_cap);
     FEC_MARK(ws, "k_flatten_stats", st);
-    k_kept<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.csize, ws.cmin, ws.frames, prm.nf,
+    launch(k_kept, grid1, 256, 0, st, ws.plan, ws.parent, ws.csize, ws.cmin, ws.frames, prm.nf,
                                   ws.kept_key_a(), ws.kept_val_a(), ws.rank_bits);
     FEC_MARK(ws, "k_kept", st);
     return cudaGetLastError();
@@ -1219,18 +1229,18 @@ cudaError_t enqueue_labels(Workspace &ws, const Params &prm, int32_t *labels, bo
 {
     const int grid1 = grid_for(ws, prm.n, 256, 8);
     const uint64_t words = ((uint64_t)prm.n + 31) / 32;
-    k_rankscan<<<grid_for(ws, words, kRankTileWords, 4), kRankThreads, 0, st>>>(
+    launch(k_rankscan, grid_for(ws, words, kRankTileWords, 4), kRankThreads, 0, st,
         ws.plan, prm, ws.rank_bits, ws.rank_prefix, ws.rank_status);
     FEC_MARK(ws, "k_rankscan", st);
-    k_rank<<<grid_for(ws, prm.n, 256, 4), 256, 0, st>>>(ws.plan, ws.kept_key_a(), ws.kept_val_a(),
+    launch(k_rank, grid_for(ws, prm.n, 256, 4), 256, 0, st, ws.plan, ws.kept_key_a(), ws.kept_val_a(),
                                                         ws.rank_bits, ws.rank_prefix, ws.frames,
                                                         prm.nf, ws.crank);
     FEC_MARK(ws, "k_rank", st);
     // sorted original indices: the 32-bit values, or the low half of the packed payloads
     int32_t *sclab = (int32_t *)ws.csize;  // component sizes are no longer needed
-    k_sclabel<<<grid1, 256, 0, st>>>(ws.plan, ws.parent, ws.crank, sclab, labels, fill ? prm.rows : 0u);
+    launch(k_sclabel, grid1, 256, 0, st, ws.plan, ws.parent, ws.crank, sclab, labels, fill ? prm.rows : 0u);
     FEC_MARK(ws, "k_sclabel", st);
-    k_labels<<<grid_for(ws, prm.n, 2048, 8), 256, 0, st>>>(ws.plan, (const uint32_t *)ws.vals_a,
+    launch(k_labels, grid_for(ws, prm.n, 2048, 8), 256, 0, st, ws.plan, (const uint32_t *)ws.vals_a,
                                          (const uint32_t *)ws.vals_b, prm.packed ? 2u : 1u, ws.sc_of,
                                          sclab, labels, prm.rows);
     FEC_MARK(ws, "k_labels", st);
