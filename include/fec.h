@@ -53,7 +53,8 @@ typedef enum {
     FEC_ERR_NOT_CONVERGED = 6,  /* a bounded device loop hit its iteration cap */
     FEC_ERR_NOT_READY = 7,      /* fec_serve_poll: request still queued or running */
     FEC_ERR_BUSY = 8,           /* fec_serve_submit: request can never fit the budget / queue full */
-    FEC_ERR_TIMEOUT = 9         /* serving: the request's deadline passed before it started */
+    FEC_ERR_TIMEOUT = 9,        /* serving: the request's deadline passed before it started */
+    FEC_ERR_INTERNAL = 10       /* debug builds (FEC_DEBUG) only: a device bounds check failed */
 } fec_status;
 
 typedef struct fec_ctx fec_ctx;

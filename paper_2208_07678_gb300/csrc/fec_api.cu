@@ -222,6 +222,7 @@ __global__ void k_summary(const Plan *plan, Summary *out)
 
 fec_status status_from_bits(uint32_t s)
 {
+    if (s & ST_DEBUG_BOUNDS) return FEC_ERR_INTERNAL;
     if (s & ST_NONFINITE) return FEC_ERR_NONFINITE;
     if (s & (ST_OUT_OF_RANGE | ST_KEY_OVERFLOW)) return FEC_ERR_OUT_OF_RANGE;
     if (s & (ST_WAIT_TIMEOUT | ST_UNION_CAP)) return FEC_ERR_NOT_CONVERGED;
@@ -675,6 +676,7 @@ const char *fec_status_string(fec_status s)
     case FEC_ERR_NOT_READY: return "FEC_ERR_NOT_READY";
     case FEC_ERR_BUSY: return "FEC_ERR_BUSY";
     case FEC_ERR_TIMEOUT: return "FEC_ERR_TIMEOUT";
+    case FEC_ERR_INTERNAL: return "FEC_ERR_INTERNAL";
     }
     return "FEC_ERR_UNKNOWN";
 }

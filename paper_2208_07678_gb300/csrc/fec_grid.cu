@@ -842,8 +842,14 @@ __global__ void __launch_bounds__(256)
         if (e - s > prm.big_subcell) {
             // medium sub-cells from the front of the list, huge ones from its middle
             // (at most n/65 and n/2049 of them)
-            if (e - s > (uint32_t)kHugeSubcell) big[plan->sort.n / 2 + atomicAdd(&plan->n_huge, 1u)] = a;
-            else big[atomicAdd(&plan->n_big, 1u)] = a;
+            if (e - s > (uint32_t)kHugeSubcell) {
+                const uint32_t j = atomicAdd(&plan->n_huge, 1u);
+                if (FEC_IN_BOUNDS(&plan->status, j, plan->sort.n / (kHugeSubcell + 1) + 1))
+                    big[plan->sort.n / 2 + j] = a;
+            } else {
+                const uint32_t j = atomicAdd(&plan->n_big, 1u);
+                if (FEC_IN_BOUNDS(&plan->status, j, plan->sort.n / 2)) big[j] = a;
+            }
             continue;
         }
         SubBox b;

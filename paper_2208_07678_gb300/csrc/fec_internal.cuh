@@ -38,11 +38,12 @@ enum : uint32_t {
     ST_UNION_CAP = 1u << 4,        // a union/find loop hit its cap
     ST_SIZE_OVERFLOW = 1u << 5,    // a device count exceeded its buffer
     ST_QUEUE_OVERFLOW = 1u << 6,   // more boundary edges / pairs than the lists hold
+    ST_DEBUG_BOUNDS = 1u << 7,     // FEC_DEBUG builds: a device bounds check failed
 };
 // Status bits after which a call's remaining kernels return at once: a wait
 // or union loop gave up, or a device count went out of range, so later
 // stages would index through wrong offsets.
-constexpr uint32_t kAbortBits = ST_WAIT_TIMEOUT | ST_UNION_CAP | ST_SIZE_OVERFLOW;
+constexpr uint32_t kAbortBits = ST_WAIT_TIMEOUT | ST_UNION_CAP | ST_SIZE_OVERFLOW | ST_DEBUG_BOUNDS;
 
 // Work counters of the union step (Plan::ctr).
 enum {
@@ -429,6 +430,29 @@ __device__ __forceinline__ bool block_aborted(const uint32_t *status)
 {
     return __syncthreads_or(threadIdx.x == 0 && call_aborted(status)) != 0;
 }
+
+// Debug builds (-DFEC_DEBUG=1, libfec_debug.so) check the indices of the
+// gathers and scatters that depend on device-computed offsets.
+// FEC_IN_BOUNDS(status, i, n) is true when i < n; otherwise it sets
+// ST_DEBUG_BOUNDS in the call's status (the call ends with FEC_ERR_INTERNAL
+// and its later kernels return at once) and the caller skips the access.
+// Release builds compile it to `true` and evaluate neither i nor n.
+#ifndef FEC_DEBUG
+#define FEC_DEBUG 0
+#endif
+#if FEC_DEBUG
+__device__ __forceinline__ bool debug_in_bounds(uint32_t *status, unsigned long long i,
+                                                unsigned long long n)
+{
+    if (i < n) return true;
+    atomicOr(status, ST_DEBUG_BOUNDS);
+    return false;
+}
+#define FEC_IN_BOUNDS(status, i, n) \
+    ::fec::debug_in_bounds((status), (unsigned long long)(i), (unsigned long long)(n))
+#else
+#define FEC_IN_BOUNDS(status, i, n) true
+#endif
 
 // Programmatic dependent launch.  Kernels are launched (launch() below) so
 // that the launch of a kernel is prepared while the previous kernel of the

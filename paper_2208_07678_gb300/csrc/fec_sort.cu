@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks)
             if (li < seg_n) {
                 const uint32_t d = dig[r];
                 const uint32_t lp = S.excl[d] + S.wcnt[warp][d] + lrank[r];
+                if (!FEC_IN_BOUNDS(status, lp, kSortTile)) continue;
                 S.keys[lp] = key[r];
                 S.vals[lp] = val[r];
             }

@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(256, 4)
             const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, b1, b2, plan, sbase, nslab,
                                         next_same, cell_key, slab_lo, slab_hi, col_lo, col_hi, f);
             for (int t = 0; t < nf; ++t) {
+                if (!FEC_IN_BOUNDS(&plan->status, f[t], M) || !FEC_IN_BOUNDS(&plan->status, K, 13)) break;
                 const uint32_t q = f[t], first = cell_sc[q];
                 nb_first[(size_t)c * 13 + K] = first;
                 const unsigned long long nk = cell_key[q];
@@ -469,6 +470,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     RegionSmem &S = *reinterpret_cast<RegionSmem *>(region_smem);
     if (block_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
+    const uint32_t Ms = plan->M_s;  // read in debug builds only
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     uint32_t *status = &plan->status;
@@ -503,6 +505,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         const uint32_t c_lo = S.region, c_hi = S.rend;
         if (c_lo >= M) break;
         const uint32_t s0 = cell_sc[c_lo], s1 = cell_sc[c_hi], ns = s1 - s0;
+        if (!FEC_IN_BOUNDS(status, ns, kRegionSubs + 1)) break;  // block-uniform
         for (uint32_t i = tid; i < ns; i += blockDim.x) S.par[i] = (uint16_t)i;
         for (int i = tid; i < kRegionBuf; i += blockDim.x) {
             S.ebuf[i] = make_uint2(0xffffffffu, 0xffffffffu);
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                         const uint32_t nm = ((mw >> (8 * (hl & 3))) & 31u) << 3;
                         uint32_t rest = occ;
                         for (uint32_t j = ci - cnt, b = first; j < ci; ++j, ++b) {
+                            if (!FEC_IN_BOUNDS(status, j, 112)) break;
                             S.nsub[cs][j] = b;
                             S.ninfo[cs][j] = (uint8_t)(nm | (__ffs(rest) - 1));
                             rest &= rest - 1;
@@ -619,7 +623,8 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
             uint32_t a = 0, b = 0;
             int dec = 0;
             bool local = true;
-            if ((uint32_t)lane < mq) {
+            if ((uint32_t)lane < mq && FEC_IN_BOUNDS(status, S.qa[w][lane] - s0, ns) &&
+                FEC_IN_BOUNDS(status, S.qb[w][lane], Ms)) {
                 a = S.qa[w][lane];
                 b = S.qb[w][lane];
                 local = b - s0 < ns;
@@ -700,7 +705,8 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     const uint32_t v = my_scratch[w * wcap + i];
                     la = v & 0xffffu;
                     lb = v >> 16;
-                    live = s_find(vpar, la) != s_find(vpar, lb);
+                    live = FEC_IN_BOUNDS(status, la, ns) && FEC_IN_BOUNDS(status, lb, ns) &&
+                           s_find(vpar, la) != s_find(vpar, lb);
                 }
                 uint32_t lmask = __ballot_sync(0xffffffffu, live);
                 while (lmask) {
@@ -773,6 +779,8 @@ __global__ void __launch_bounds__(256)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
         const uint2 e = edges[i];
         if (e.x == 0xffffffffu) continue;  // unused buffer slot
+        if (!FEC_IN_BOUNDS(&plan->status, e.x, plan->M_s) || !FEC_IN_BOUNDS(&plan->status, e.y, plan->M_s))
+            continue;
         uint32_t ra = parent[e.x], rb = parent[e.y];
         if (ra == rb) continue;
         if (ra > rb) {
@@ -822,7 +830,8 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
         if (i < nq) {
             pr = pairq[i];
             bool ok = true;
-            live = pr.x != 0xffffffffu && uf_find(parent, pr.x, cap, ok) != uf_find(parent, pr.y, cap, ok);
+            live = pr.x != 0xffffffffu && FEC_IN_BOUNDS(status, pr.x, plan->M_s) &&
+                   FEC_IN_BOUNDS(status, pr.y, plan->M_s) && uf_find(parent, pr.x, cap, ok) != uf_find(parent, pr.y, cap, ok);
             if (!ok) atomicOr(status, ST_UNION_CAP);
             if (!live) ++n_same;
         }
@@ -884,6 +893,7 @@ __global__ void __launch_bounds__(256, 4)
                     found = true;
                     break;
                 }
+                if (!FEC_IN_BOUNDS(&plan->status, p, M)) break;
                 r = p;
             }
             if (!found) atomicOr(&plan->status, ST_UNION_CAP);
@@ -957,7 +967,8 @@ __global__ void __launch_bounds__(256)
             const uint32_t row = cmin[a];
             const uint32_t f = frame_of_row(fr, nf, row);
             const long long s = (long long)csize[a];
-            keep = s >= fr[f].min_size && s <= fr[f].max_size;
+            keep = s >= fr[f].min_size && s <= fr[f].max_size &&
+                   FEC_IN_BOUNDS(&plan->status, row - fr[f].in_off, fr[f].n);
             pos = fr[f].pos_off + (row - fr[f].in_off);
             if (keep) {
                 atomicOr(rank_bits + (pos >> 5), 1u << (pos & 31u));
@@ -970,7 +981,7 @@ __global__ void __launch_bounds__(256)
         uint32_t slot = 0;
         if (lane == leader) slot = atomicAdd(&plan->kept.n, (uint32_t)__popc(mask));
         slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(mask & lanemask_lt());
-        if (keep) {
+        if (keep && FEC_IN_BOUNDS(&plan->status, slot, M)) {
             kept_key[slot] = pos;
             kept_val[slot] = a;
         }
@@ -1086,6 +1097,9 @@ __global__ void __launch_bounds__(256)
     const uint32_t k = plan->kept.n;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         const uint32_t pos = kept_key[t];
+        if (!FEC_IN_BOUNDS(&plan->status, pos, plan->sort.n) ||
+            !FEC_IN_BOUNDS(&plan->status, kept_val[t], plan->M_s))
+            continue;
         uint32_t r = bits_before(rank_bits, rank_prefix, pos);
         if (nf > 1) r -= bits_before(rank_bits, rank_prefix, fr[frame_of_pos(fr, nf, pos)].pos_off);
         crank[kept_val[t]] = (int32_t)r;
@@ -1103,7 +1117,7 @@ __global__ void __launch_bounds__(256)
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_s;
     for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < M; a += gridDim.x * blockDim.x)
-        sclab[a] = crank[parent[a]];
+        if (FEC_IN_BOUNDS(&plan->status, parent[a], M)) sclab[a] = crank[parent[a]];
     // 16-byte stores when the output is 16-byte aligned (a batch frame's
     // labels start anywhere), else 4-byte stores
     const uint32_t n4 = (reinterpret_cast<uintptr_t>(labels) & 15) ? 0u : n / 4;  // n: labels to fill
@@ -1140,7 +1154,7 @@ __global__ void __launch_bounds__(256)
         bool any = false;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            l[t] = sclab[sc[t]];
+            l[t] = FEC_IN_BOUNDS(&plan->status, sc[t], plan->M_s) ? sclab[sc[t]] : -1;
             any |= l[t] >= 0;
         }
         if (!any) continue;
@@ -1169,7 +1183,7 @@ __global__ void __launch_bounds__(256)
     }
     for (uint32_t p = n8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += gridDim.x * blockDim.x) {
-        const int32_t l = sclab[sc_of[p]];
+        const int32_t l = FEC_IN_BOUNDS(&plan->status, sc_of[p], plan->M_s) ? sclab[sc_of[p]] : -1;
         const uint32_t i = idx[(size_t)p * idx_stride];
         if (l >= 0 && i < rows) labels[i] = l;
     }

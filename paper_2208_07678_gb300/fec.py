@@ -24,7 +24,7 @@ FEC_MAX_POINTS = 1 << 30
 
 STATUS = {0: "FEC_OK", 1: "FEC_ERR_INVALID_ARG", 2: "FEC_ERR_NONFINITE", 3: "FEC_ERR_OUT_OF_RANGE",
           4: "FEC_ERR_OOM", 5: "FEC_ERR_CUDA", 6: "FEC_ERR_NOT_CONVERGED", 7: "FEC_ERR_NOT_READY",
-          8: "FEC_ERR_BUSY", 9: "FEC_ERR_TIMEOUT"}
+          8: "FEC_ERR_BUSY", 9: "FEC_ERR_TIMEOUT", 10: "FEC_ERR_INTERNAL"}
 FEC_OK, FEC_ERR_NOT_READY, FEC_ERR_TIMEOUT = 0, 7, 9
 
 # Every function the header declares (checked by the CPU tests against include/fec.h).
@@ -78,20 +78,28 @@ class fec_trace_entry(ctypes.Structure):
 _lib = None
 
 
+def debug_library() -> bool:
+    """True when the environment selects the bounds-checked debug build
+    (FEC_LIBRARY=debug; for debugging and its own tests only)."""
+    return os.environ.get("FEC_LIBRARY", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_library() else _build.LIB
 
 
 def load(build_if_missing: bool = False):
-    """Load libfec.so (optionally building it first).  Raises if absent."""
+    """Load libfec.so, or libfec_debug.so when FEC_LIBRARY=debug (optionally
+    building it first).  Raises if absent."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
+    path = library_path()
+    if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
-        _build.build()
-    lib = ctypes.CDLL(_build.LIB)
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        _build.build(debug=debug_library())
+    lib = ctypes.CDLL(path)
     vp, i64, i32p, f32p = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p
     lib.fec_create.argtypes = [ctypes.POINTER(fec_options), ctypes.POINTER(vp)]
     lib.fec_create.restype = ctypes.c_int

@@ -47,6 +47,17 @@ def test_exports_match_nm(lib):
     assert header_functions() <= exported
 
 
+def test_debug_build_exports_the_same_functions():
+    """The bounds-checked debug library (-DFEC_DEBUG=1) builds and exports
+    every declared function, like the release library."""
+    import subprocess
+
+    path = libbuild.build(debug=True)
+    assert path == libbuild.LIB_DEBUG and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert header_functions() <= set(re.findall(r"\bT (fec_[a-z_0-9]+)", out))
+
+
 def test_status_strings(lib):
     for code, name in fec.STATUS.items():
         assert fec.fec_status_string(code) == name
