@@ -247,8 +247,8 @@ int64_t fec_workspace_bytes(int64_t n, float d);
  * the process exits), so it needs no context and allocates nothing.
  *   xyz, labels  caller-owned, host or device memory, as for fec_cluster.
  *   n            at most FEC_NOALLOC_MAX_POINTS; larger n gives
- *                FEC_ERR_INVALID_ARG.  A cloud longer than 65,536 grid cells
- *                (of side about d) along its longest axis gives
+ *                FEC_ERR_INVALID_ARG.  A cloud longer than 1,048,576 grid
+ *                cells (of side about d) along its longest axis gives
  *                FEC_ERR_OUT_OF_RANGE, and one that needs more boundary
  *                lists than the array holds gives FEC_ERR_OOM.
  *   cuda_stream  cudaStream_t to run on (NULL = the default stream).

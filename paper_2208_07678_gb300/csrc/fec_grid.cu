@@ -321,14 +321,18 @@ __global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr
     }
     __syncthreads();
     if (s_stop) return;
-    // each frame's slab entries (its major cell coordinates), laid out in
-    // frame order: an exclusive scan in chunks of 256 frames
+    // each frame's slab entries (the brick rows of its major cell
+    // coordinates), laid out in frame order: an exclusive scan in chunks of
+    // 256 frames
     const int p0 = s_perm0;
+    CellKeyLayout L;
+    L.load(plan);
     uint32_t carry = 0;
     for (uint32_t c0 = 0; c0 < prm.nf; c0 += blockDim.x) {
         const uint32_t f = c0 + t;
         uint32_t ns = 0;
-        if (f < prm.nf) ns = (uint32_t)(((int64_t)fr[f].hi[p0] - fr[f].lo[p0]) / prm.S) + 1u;
+        if (f < prm.nf)
+            ns = (uint32_t)L.slab_of((unsigned long long)(((int64_t)fr[f].hi[p0] - fr[f].lo[p0]) / prm.S)) + 1u;
         s_scan[t] = ns;
         __syncthreads();
         for (int o = 1; o < 256; o <<= 1) {
@@ -1039,9 +1043,10 @@ __global__ void __launch_bounds__(256)
                     gridDim.x - huge_blocks);
 }
 
-// a3: slab index over the major cell coordinate: cells of slab x occupy
-// [slab_lo[x], slab_hi[x]) of the sorted cell array (empty: lo == hi == 0);
-// and, when it fits, the dense column index over (c_p0, c_p1) the same way.
+// a3: slab index over the brick rows of the major cell coordinate (see
+// CellKeyLayout): cells of slab x occupy [slab_lo[x], slab_hi[x]) of the
+// sorted cell array (empty: lo == hi == 0); and, when it fits, the dense
+// column index over (c_p0, c_p1) (the cell key above c_p2) the same way.
 __global__ void __launch_bounds__(256)
     k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
             const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
@@ -1053,8 +1058,10 @@ __global__ void __launch_bounds__(256)
     grid_enter();
     if (call_aborted(&plan->status)) return;
     const uint32_t M = plan->M_c;
-    const uint32_t b2 = plan->bits[2];
-    const uint32_t sh = plan->bits[1] + b2;
+    CellKeyLayout L;
+    L.load(plan);
+    const uint32_t b2 = L.b2;
+    const uint32_t sh = L.b2 + L.b1 + L.B0;  // key bits below the brick row
     const bool cols = plan->use_cols != 0;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
         const unsigned long long k = cell_key[c];

@@ -131,7 +131,7 @@ struct __align__(16) Frame {
     int32_t lo[3];       // bounding box of q per original axis (device)
     uint32_t kept;       // kept clusters (device)
     int32_t hi[3];
-    uint32_t nslab;      // slab-index entries: the frame's largest major cell coordinate + 1 (device)
+    uint32_t nslab;      // slab-index entries: brick rows of the frame's major cell coordinate (device)
     uint32_t slab_base;  // first slab-index entry of the frame (device)
     uint32_t pad[3];
 };
@@ -249,28 +249,79 @@ __device__ __forceinline__ int quantize1(float x, int32_t &q)
     return 0;
 }
 
+// Layout of a cell key (the sort key without its 3 sub-cell bits).  With
+// b0, b1, b2 bits of cell coordinate along the permuted axes p0 (major), p1,
+// p2 (minor), the columns (c0, c1) are grouped in bricks of 2^B0 x 2^B1
+// columns (B = FEC_KEY_BRICK, less on an axis with fewer bits):
+//   [ c0 >> B0 | c1 >> B1 | c0 mod 2^B0 | c1 mod 2^B1 | c2 ]
+// so that a run of consecutive cells (a region of the neighbour step) is a
+// compact block of columns instead of a one-cell-thick slice along p0: fewer
+// neighbour pairs cross regions.  A column's cells stay consecutive (c2 is
+// the lowest field), and the "slab" of c0 is the key range of its brick row,
+// c0 >> B0.
+#ifndef FEC_KEY_BRICK
+#define FEC_KEY_BRICK 4
+#endif
+struct CellKeyLayout {
+    uint32_t b0, b1, b2, B0, B1;
+    __device__ __forceinline__ void load(const Plan *plan)
+    {
+        b0 = plan->bits[0];
+        b1 = plan->bits[1];
+        b2 = plan->bits[2];
+        B0 = min(b0, (uint32_t)FEC_KEY_BRICK);
+        B1 = min(b1, (uint32_t)FEC_KEY_BRICK);
+    }
+    // cell key of column (c0, c1) at c2 = 0
+    __device__ __forceinline__ unsigned long long column(unsigned long long c0, unsigned long long c1) const
+    {
+        const unsigned long long m0 = (1ull << B0) - 1, m1 = (1ull << B1) - 1;
+        return ((c0 >> B0) << (b2 + b1 + B0)) | ((c1 >> B1) << (b2 + B1 + B0)) | ((c0 & m0) << (b2 + B1)) |
+               ((c1 & m1) << b2);
+    }
+    __device__ __forceinline__ void decode(unsigned long long ck, unsigned long long &c0,
+                                           unsigned long long &c1, unsigned long long &c2) const
+    {
+        const unsigned long long m0 = (1ull << B0) - 1, m1 = (1ull << B1) - 1;
+        c2 = ck & ((1ull << b2) - 1);
+        c1 = (((ck >> (b2 + B1 + B0)) & ((1ull << (b1 - B1)) - 1)) << B1) | ((ck >> b2) & m1);
+        c0 = ((ck >> (b2 + b1 + B0)) << B0) | ((ck >> (b2 + B1)) & m0);
+    }
+    // slab (brick row) of a major coordinate
+    __device__ __forceinline__ unsigned long long slab_of(unsigned long long c0) const { return c0 >> B0; }
+};
+
 // Grid coordinates of a quantised point under the plan.  The sort key is
-// [c_p0 | c_p1 | c_p2 | s_p0 s_p1 s_p2] (c = cell coordinate along the
-// permuted axes, major first; s = which half of the cell), so every original
-// axis a has a fixed place in it: its cell coordinate at bit ksh[a] (kwid[a]
-// bits wide) and its half at bit kbit[a].  These are resolved once in load(), so
-// a point's key is a few shifts with no per-point axis selection.
+// the cell key (CellKeyLayout) above [s_p0 s_p1 s_p2] (s = which half of the
+// cell along each permuted axis), so every original axis a has fixed places
+// in it: the low lw[a] bits of its cell coordinate at bit lsh[a], the other
+// hw[a] bits at bit hsh[a], and its half at bit kbit[a].  These are resolved
+// once in load(), so a point's key is a few shifts with no per-point axis
+// selection.
 struct GridMap {
     int32_t lo[3];
-    uint32_t ksh[3], kbit[3], kwid[3];
+    uint32_t lsh[3], hsh[3], lw[3], hw[3], kbit[3];
     int32_t S, h;
     uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
 
     __device__ __forceinline__ void load(const Plan *plan, const Params &prm, const Frame &fr)
     {
-        const uint32_t b0 = plan->bits[0], b1 = plan->bits[1], b2 = plan->bits[2];
+        CellKeyLayout L;
+        L.load(plan);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {  // constant indices only (no local memory)
             lo[a] = fr.lo[a];
             const int p = plan->perm[0] == a ? 0 : (plan->perm[1] == a ? 1 : 2);
-            ksh[a] = 3u + (p == 0 ? b1 + b2 : (p == 1 ? b2 : 0u));
+            // p0: low B0 bits at b2 + B1, the rest at b2 + b1 + B0; p1: low B1
+            // bits at b2, the rest at b2 + B1 + B0; p2: all b2 bits at 0
+            lw[a] = p == 0 ? L.B0 : (p == 1 ? L.B1 : L.b2);
+            hw[a] = p == 0 ? L.b0 - L.B0 : (p == 1 ? L.b1 - L.B1 : 0u);
+            lsh[a] = 3u + (p == 0 ? L.b2 + L.B1 : (p == 1 ? L.b2 : 0u));
+            hsh[a] = 3u + (p == 0 ? L.b2 + L.b1 + L.B0 : (p == 1 ? L.b2 + L.B1 + L.B0 : 0u));
+            // an empty field holds zeros: shift by 0, never by the key's width
+            if (lw[a] == 0) lsh[a] = 0;
+            if (hw[a] == 0) hsh[a] = 0;
             kbit[a] = 2u - (uint32_t)p;
-            kwid[a] = p == 0 ? b0 : (p == 1 ? b1 : b2);
         }
         S = prm.S;
         h = prm.h;
@@ -300,7 +351,8 @@ struct GridMap {
         KeyT k = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            k |= ((KeyT)c[a] << ksh[a]) | ((KeyT)(off[a] >= (uint32_t)h ? 1u : 0u) << kbit[a]);
+            k |= ((KeyT)(c[a] & ((1u << lw[a]) - 1u)) << lsh[a]) | ((KeyT)(c[a] >> lw[a]) << hsh[a]) |
+                 ((KeyT)(off[a] >= (uint32_t)h ? 1u : 0u) << kbit[a]);
         return k;
     }
     // Sort payload of the packed layout: the original index in the low 32
@@ -317,7 +369,8 @@ struct GridMap {
     {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const uint32_t c = (uint32_t)((key >> ksh[a]) & (((KeyT)1 << kwid[a]) - 1));
+            const uint32_t c = (uint32_t)((key >> lsh[a]) & (((KeyT)1 << lw[a]) - 1)) |
+                               ((uint32_t)((key >> hsh[a]) & (((KeyT)1 << hw[a]) - 1)) << lw[a]);
             q[a] = lo[a] + (int32_t)(c * (uint32_t)S) + (int32_t)((v >> (32 + 10 * a)) & 1023u);
         }
     }

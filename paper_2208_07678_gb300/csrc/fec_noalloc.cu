@@ -30,7 +30,7 @@ fec_status status_from_bits(uint32_t s);  // fec_api.cu
 namespace {
 
 constexpr int64_t kMaxPoints = FEC_NOALLOC_MAX_POINTS;
-constexpr uint32_t kSlabCap = 65536;                 // major-axis cells the slab index covers
+constexpr uint32_t kSlabCap = 65536;                 // slab entries (brick rows of 16 major-axis cells)
 constexpr size_t kScratchBytes = (size_t)16 << 20;   // 16 MiB per device
 constexpr int kMaxDevices = 64;
 

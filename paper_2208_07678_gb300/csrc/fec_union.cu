@@ -194,10 +194,11 @@ __device__ __forceinline__ int box_decide(const SubBox &A, const SubBox &B, uint
 
 // Cells of column (n0, n1) with minor coordinate in [z_lo, z_hi] (at most
 // 3): through the dense column index when the plan enables it, else by
-// binary search in slab n0.  Returns how many were written to out[].
+// binary search in the slab (brick row) of n0.  Returns how many were
+// written to out[].
 __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long long n1,
                                             unsigned long long z_lo, unsigned long long z_hi,
-                                            uint32_t b1, uint32_t b2, const Plan *plan,
+                                            const CellKeyLayout &L, const Plan *plan,
                                             uint32_t slab_base, uint32_t nslab,
                                             const unsigned long long *__restrict__ cell_key,
                                             const uint32_t *__restrict__ slab_lo,
@@ -206,16 +207,17 @@ __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long
                                             const uint32_t *__restrict__ col_hi, uint32_t out[3])
 {
     uint32_t lo, end;
+    const unsigned long long colkey = L.column(n0, n1);
     if (plan->use_cols) {
-        const unsigned long long col = (n0 << b1) | n1;
+        const unsigned long long col = colkey >> L.b2;
         lo = col_lo[col];
         end = col_hi[col];
     } else {
-        if (n0 >= nslab) return 0;  // beyond the frame's slabs
-        lo = slab_lo[slab_base + n0];
-        end = slab_hi[slab_base + n0];
+        const unsigned long long x = L.slab_of(n0);
+        if (x >= nslab) return 0;  // beyond the frame's slabs
+        lo = slab_lo[slab_base + x];
+        end = slab_hi[slab_base + x];
     }
-    const unsigned long long colkey = (n0 << (b1 + b2)) | (n1 << b2);
     const unsigned long long tlo = colkey | z_lo, thi = colkey | z_hi;
     uint32_t hi = end;
     while (lo < hi) {
@@ -237,7 +239,7 @@ __device__ __forceinline__ int column_cells(unsigned long long n0, unsigned long
 // lane 4 takes (0,0,+1), the next cell of the same column (of the same
 // frame).  Each lane returns its cells in f[0..2] and their count.
 __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, unsigned long long ck,
-                                            uint32_t b1, uint32_t b2, const Plan *plan,
+                                            const CellKeyLayout &L, const Plan *plan,
                                             uint32_t slab_base, uint32_t nslab, bool next_same,
                                             const unsigned long long *__restrict__ cell_key,
                                             const uint32_t *__restrict__ slab_lo,
@@ -245,8 +247,9 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
                                             const uint32_t *__restrict__ col_lo,
                                             const uint32_t *__restrict__ col_hi, uint32_t f[3])
 {
-    const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
-    const unsigned long long c0 = ck >> (b1 + b2), c1 = (ck >> b2) & m1, c2 = ck & m2;
+    const unsigned long long m1 = (1ull << L.b1) - 1, m2 = (1ull << L.b2) - 1;
+    unsigned long long c0, c1, c2;
+    L.decode(ck, c0, c1, c2);
     if (lane == 4) {
         if (c2 < m2 && c + 1 < M && next_same && cell_key[c + 1] == ck + 1) {
             f[0] = c + 1;
@@ -258,10 +261,10 @@ __device__ __forceinline__ int stencil_lane(int lane, uint32_t c, uint32_t M, un
     const long long d0 = lane == 0 ? 0 : 1;
     const long long d1 = lane == 0 ? 1 : lane - 2;
     const long long n0 = (long long)c0 + d0, n1 = (long long)c1 + d1;
-    const unsigned long long m0 = (1ull << plan->bits[0]) - 1;
+    const unsigned long long m0 = (1ull << L.b0) - 1;
     if (n1 < 0 || (unsigned long long)n1 > m1 || (unsigned long long)n0 > m0) return 0;
     return column_cells((unsigned long long)n0, (unsigned long long)n1, c2 > 0 ? c2 - 1 : 0,
-                        c2 < m2 ? c2 + 1 : m2, b1, b2, plan, slab_base, nslab, cell_key, slab_lo,
+                        c2 < m2 ? c2 + 1 : m2, L, plan, slab_base, nslab, cell_key, slab_lo,
                         slab_hi, col_lo, col_hi, f);
 }
 
@@ -314,10 +317,12 @@ __global__ void __launch_bounds__(256, 4)
          i += gridDim.x * blockDim.x)
         edge_set[i] = ~0ull;
     const uint32_t M = plan->M_c;
-    const uint32_t b1 = plan->bits[1], b2 = plan->bits[2];
-    const unsigned long long m1 = (1ull << b1) - 1, m2 = (1ull << b2) - 1;
+    CellKeyLayout L;
+    L.load(plan);
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
         const unsigned long long ck = cell_key[c];
+        unsigned long long e0, e1, e2;  // the cell's coordinates
+        L.decode(ck, e0, e1, e2);
         uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int K = 0;
         // the cell's frame: its part of the slab index; the next cell must be of it too
@@ -327,16 +332,17 @@ __global__ void __launch_bounds__(256, 4)
 #pragma unroll
         for (int col = 0; col < 5; ++col) {
             uint32_t f[3];
-            const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, b1, b2, plan, sbase, nslab,
+            const int nf = stencil_lane(col == 0 ? 4 : col - 1, c, M, ck, L, plan, sbase, nslab,
                                         next_same, cell_key, slab_lo, slab_hi, col_lo, col_hi, f);
             for (int t = 0; t < nf; ++t) {
                 if (!FEC_IN_BOUNDS(&plan->status, f[t], M) || !FEC_IN_BOUNDS(&plan->status, K, 13)) break;
                 const uint32_t q = f[t], first = cell_sc[q];
                 nb_first[(size_t)c * 13 + K] = first;
-                const unsigned long long nk = cell_key[q];
-                const long long d0 = (long long)(nk >> (b1 + b2)) - (long long)(ck >> (b1 + b2));
-                const long long d1 = (long long)((nk >> b2) & m1) - (long long)((ck >> b2) & m1);
-                const long long d2 = (long long)(nk & m2) - (long long)(ck & m2);
+                unsigned long long n0, n1, n2;
+                L.decode(cell_key[q], n0, n1, n2);
+                const long long d0 = (long long)n0 - (long long)e0;
+                const long long d1 = (long long)n1 - (long long)e1;
+                const long long d2 = (long long)n2 - (long long)e2;
                 const uint32_t plus = (d0 == 1 ? 4u : 0u) | (d1 == 1 ? 2u : 0u) | (d2 == 1 ? 1u : 0u);
                 const uint32_t minus = (d1 == -1 ? 2u : 0u) | (d2 == -1 ? 1u : 0u);
                 // K < 13, so the word indices below stay in range (unrolled: registers)
@@ -375,6 +381,14 @@ __global__ void __launch_bounds__(256, 4)
 // Only boundary edges and cross-region pairs leave the block, through
 // shared-memory buffers flushed in chunks.
 // ---------------------------------------------------------------------------
+#ifndef FEC_REGION_TAIL_DIV
+#define FEC_REGION_TAIL_DIV 2
+#endif
+#ifndef FEC_REGION_TAIL_ROUNDS
+#define FEC_REGION_TAIL_ROUNDS 1
+#endif
+constexpr uint32_t kRegionTailDiv = FEC_REGION_TAIL_DIV;
+constexpr uint32_t kRegionTailRounds = FEC_REGION_TAIL_ROUNDS;
 constexpr int kRegionCells = (int)kRegionCellsPerBlock;
 constexpr int kRegionWarps = kRegionThreads / 32;
 constexpr int kRegionSubs = 8 * kRegionCells;
@@ -493,13 +507,19 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     for (;;) {
         if (tid == 0) {
             // region size: kRegionCells, or fewer cells when the cloud has too
-            // few cells to give every block two regions
+            // few cells to give every block two regions.  The last
+            // kRegionTailRounds * grid full regions' worth of cells is cut into
+            // regions kRegionTailDiv times smaller, so that blocks finish together.
             const uint32_t rc =
                 min(prm.region_cells, max(kRegionMinCells, M / (2u * gridDim.x)));
+            const uint32_t rt = max(kRegionMinCells, rc / kRegionTailDiv);
+            const uint64_t tail = (uint64_t)kRegionTailRounds * gridDim.x * rc;
+            const uint64_t full = M > tail ? (M - tail) / rc : 0;  // full-size regions
             const uint32_t r = atomicAdd(&plan->region_counter, 1u);
-            const uint64_t lo = (uint64_t)r * rc;
+            const uint64_t lo = r < full ? (uint64_t)r * rc : full * rc + (uint64_t)(r - full) * rt;
+            const uint64_t hi = lo + (r < full ? rc : rt);
             S.region = lo < M ? (uint32_t)lo : M;
-            S.rend = lo < M ? min((uint32_t)lo + rc, M) : M;
+            S.rend = lo < M ? (uint32_t)(hi < M ? hi : M) : M;
         }
         __syncthreads();
         const uint32_t c_lo = S.region, c_hi = S.rend;

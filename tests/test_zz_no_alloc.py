@@ -76,18 +76,19 @@ def test_noalloc_rejects_clouds_above_its_capacity():
 
 
 def test_noalloc_reports_a_cloud_wider_than_its_slab_index():
-    """The static workspace indexes at most 65,536 grid cells along the major
-    axis: a cloud wider than that is refused with FEC_ERR_OUT_OF_RANGE (the
-    device plan sees the overflow before any key is sorted), and the next
-    call on an ordinary cloud is exact again."""
+    """The static workspace's slab index has 65,536 entries, each a row of 16
+    grid cells along the major axis (1,048,576 cells): a cloud wider than that
+    is refused with FEC_ERR_OUT_OF_RANGE (the device plan sees the overflow
+    before any key is sorted), and the next call on an ordinary cloud is
+    exact again."""
     import torch
 
     from paper_2208_07678_gb300 import build as libbuild
 
     libbuild.build()
     torch.cuda.set_device(0)
-    d = 0.05  # cells of 52 units: 65,536 of them span about 3,328 m
-    x = np.array([[0.0, 0.0, 0.0], [3500.0, 0.0, 0.0], [3500.0, 0.03125, 0.0]], np.float32)
+    d = 0.005  # cells of 6 units: 1,048,576 of them span 6,144 m
+    x = np.array([[-4000.0, 0.0, 0.0], [4000.0, 0.0, 0.0], [4000.0, 0.00390625, 0.0]], np.float32)
     lab = np.full(3, -7, np.int32)
     st, _ = fec.fec_cluster_noalloc(x.ctypes.data, 3, d, 1, fec.INT64_MAX, lab.ctypes.data)
     assert fec.STATUS[st] == "FEC_ERR_OUT_OF_RANGE"
