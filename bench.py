@@ -45,7 +45,9 @@ FALLBACK_HBM_GBS = 6800.0
 #   k_cells          key + payload 12, record 16 + sub-cell of position 4 per point;
 #                    start 4 + code 1 per sub-cell; key 8 + first sub-cell 4 per cell
 #   k_subcell_stats  record 16 per point; start 4, box 32, smallest index 4,
-#                    representative 4, parent/size/min/rank 16 per sub-cell
+#                    representative 4, parent/size/min/rank 16, code 1 per
+#                    sub-cell; key 8, first sub-cell 4, occupancy 1 per cell
+#                    (the slab index, about one entry per column, is not counted)
 #   k_region         range 4, neighbour record 32, neighbour first sub-cells 52 per
 #                    cell; box 32, representative 4, parent 4 per sub-cell
 #   k_flatten_stats  parent 4+4, count 4, smallest index 4, size/min 8 per sub-cell
@@ -56,7 +58,7 @@ KERNEL_BYTES = {
     "k_keys": lambda n, Ms, Mc: 12 * n,
     "onesweep_u32": lambda n, Ms, Mc: 24 * n,
     "k_cells": lambda n, Ms, Mc: 32 * n + 5 * Ms + 12 * Mc,
-    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 60 * Ms,
+    "k_subcell_stats": lambda n, Ms, Mc: 16 * n + 61 * Ms + 13 * Mc,
     "k_region": lambda n, Ms, Mc: 88 * Mc + 40 * Ms,
     "k_flatten_stats": lambda n, Ms, Mc: 24 * Ms,
     "k_labels": lambda n, Ms, Mc: 16 * n + 4 * Ms,

@@ -200,25 +200,11 @@ cudaError_t enqueue_back(Workspace &ws, const float *xyz, const Params &prm_in, 
     return enqueue_labels(ws, prm, labels, fill_labels, st);
 }
 
-// Small summary of a finished call, packed on the device for one copy.
-struct Summary {
-    uint32_t status, k, M_s, M_c, key_bits, pad[3];
-    unsigned long long ctr[8];
-    uint32_t front[4];  // the plan's front[] (read back after k_plan)
-};
-
-__global__ void k_summary(const Plan *plan, Summary *out)
-{
-    grid_enter();
-    if (threadIdx.x == 0) {
-        out->status = plan->status;
-        out->k = plan->kept.n;
-        out->M_s = plan->M_s;
-        out->M_c = plan->M_c;
-        out->key_bits = plan->key_bits;
-    }
-    if (threadIdx.x < 8) out->ctr[threadIdx.x] = plan->ctr[threadIdx.x];
-}
+// The summary of a finished call: the head of its plan (status, counts,
+// counters; everything before the sort control block), copied to pinned
+// host memory.
+constexpr size_t kSummaryBytes = offsetof(Plan, sort);
+using Summary = Plan;
 
 fec_status status_from_bits(uint32_t s)
 {
@@ -367,8 +353,7 @@ struct fec_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     Workspace ws;
-    Summary *summary_dev = nullptr;
-    Summary *summary_host = nullptr;  // pinned
+    Summary *summary_host = nullptr;  // pinned; its first kSummaryBytes are valid
     fec_stats last{};
     std::mutex mu;
     ServeEngine *serve = nullptr;
@@ -486,7 +471,7 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
     st.n = n;
     st.cells = s.M_c;
     st.subcells = s.M_s;
-    st.num_clusters = s.k;
+    st.num_clusters = s.kept_n;
     st.key_bits = s.key_bits;
     st.workspace_bytes = (int64_t)ctx->ws.bytes;
     st.R = prm.R;
@@ -500,7 +485,7 @@ fec_status finish(fec_ctx *ctx, int64_t n, const Params &prm, int32_t *num_clust
     st.pairs_queued = (int64_t)s.ctr[CTR_QUEUED];
     st.boundary_edges = (int64_t)s.ctr[CTR_EDGES];
     const fec_status f = status_from_bits(s.status);
-    if (f == FEC_OK && num_clusters) *num_clusters = (int32_t)s.k;
+    if (f == FEC_OK && num_clusters) *num_clusters = (int32_t)s.kept_n;
     return f;
 }
 
@@ -596,8 +581,7 @@ fec_status cluster_once(fec_ctx *ctx, const float *xyz, int64_t n, int64_t min_s
             return FEC_ERR_CUDA;
         FEC_MARK(ws, "d2h_labels", ctx->stream);
     }
-    launch(k_summary, 1, 32, 0, ctx->stream, ws.plan, ctx->summary_dev);
-    if (cudaMemcpyAsync(ctx->summary_host, ctx->summary_dev, sizeof(Summary),
+    if (cudaMemcpyAsync(ctx->summary_host, ws.plan, kSummaryBytes,
                         cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         return FEC_ERR_CUDA;
     FEC_MARK(ws, "summary", ctx->stream);
@@ -727,8 +711,7 @@ fec_status fec_create(const fec_options *opt, fec_ctx **out)
         }
         cudaGetLastError();
     }
-    if (cudaMalloc(&ctx->summary_dev, sizeof(Summary)) != cudaSuccess ||
-        cudaMallocHost(&ctx->summary_host, sizeof(Summary)) != cudaSuccess) {
+    if (cudaMallocHost(&ctx->summary_host, sizeof(Summary)) != cudaSuccess) {
         cudaGetLastError();
         fec_destroy(ctx);
         return FEC_ERR_OOM;
@@ -748,7 +731,6 @@ void fec_destroy(fec_ctx *ctx)
     ctx->trace.destroy();
     if (ctx->ws.base && ctx->stream) cudaFreeAsync(ctx->ws.base, ctx->stream);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->summary_dev) cudaFree(ctx->summary_dev);
     if (ctx->summary_host) cudaFreeHost(ctx->summary_host);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

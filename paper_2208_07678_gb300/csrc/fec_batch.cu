@@ -62,7 +62,7 @@ __global__ void k_group_result(const Plan *plan, const Frame *fr, uint32_t nf,
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         FrameResult r;
         r.status = plan->status;
-        r.k = nf == 1 ? plan->kept.n : fr[i].kept;
+        r.k = nf == 1 ? plan->kept_n : fr[i].kept;
         r.slab_need = plan->slab_need;
         r.pad = 0;
         out[batch_index[i]] = r;

@@ -63,23 +63,16 @@ __global__ void k_init(Plan *plan, Frame *fr, uint32_t nf, uint32_t *fhist, uint
             plan->region_counter = 0;
             plan->slab_need = 0;
             plan->rank_tile_counter = 0;
+            plan->bbox_done = 0;
             plan->sort.n = n;
             plan->sort.npasses = 0;
             plan->sort.key64 = 0;
             plan->sort.parity = 0;
             plan->sort.wait_cap = wait_cap;
-            plan->kept.wait_cap = wait_cap;
-            plan->kept.n = 0;
-            plan->kept.npasses = 0;
-            plan->kept.key64 = 0;
-            plan->kept.parity = 0;
+            plan->kept_n = 0;
         }
-        for (int i = t; i < kMaxPasses * kRadixBins; i += blockDim.x) (&plan->kept.hist[0][0])[i] = 0;
         if (t < 8) plan->ctr[t] = 0;
-        if (t < kMaxPasses) {
-            plan->sort.tile_counter[t] = 0;
-            plan->kept.tile_counter[t] = 0;
-        }
+        if (t < kMaxPasses) plan->sort.tile_counter[t] = 0;
     }
     const uint32_t gt = blockIdx.x * blockDim.x + t, gs = gridDim.x * blockDim.x;
     for (uint32_t f = gt; f < nf; f += gs) {
@@ -186,9 +179,115 @@ __device__ __forceinline__ void load_rows4(const float *__restrict__ xyz, uint32
     }
 }
 
+// a1: choose the axis order (largest cell extent major, smallest minor) and
+// the key layout, the same for every frame of the call (from the largest
+// extent per axis over the frames); lay out each frame's part of the slab
+// index; disable the rest of the pipeline on a data error.  Run by one
+// whole block (256 threads), the last of the bounding-box kernel, after
+// every block's boxes are in memory: the boxes are read past the L1 cache,
+// which may hold lines of the frame table from before.
+__device__ __forceinline__ void plan_body(Plan *plan, Frame *__restrict__ fr, const Params &prm)
+{
+    __shared__ uint32_t s_cm[3];
+    __shared__ uint32_t s_scan[256];
+    __shared__ int s_perm0;
+    __shared__ uint32_t s_stop;
+    const int t = threadIdx.x;
+    if (t < 3) s_cm[t] = 0;
+    if (t == 0) s_stop = (*(volatile uint32_t *)&plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) ? 1u : 0u;
+    __syncthreads();
+    // the host's 16-byte read-back of the outcome
+    auto publish = [&]() {
+        plan->front[0] = plan->status;
+        plan->front[1] = plan->sort.key64;
+        plan->front[2] = plan->sort.npasses;
+        plan->front[3] = plan->key_bits;
+    };
+    if (s_stop) {
+        if (t == 0) {
+            plan->sort.n = 0;
+            publish();
+        }
+        return;
+    }
+    for (uint32_t f = t; f < prm.nf; f += blockDim.x)
+        for (int a = 0; a < 3; ++a)
+            atomicMax(&s_cm[a], (uint32_t)(((int64_t)__ldcg(&fr[f].hi[a]) - __ldcg(&fr[f].lo[a])) / prm.S));
+    __syncthreads();
+    if (t == 0) {
+        uint32_t cm[3] = {s_cm[0], s_cm[1], s_cm[2]};
+        int perm[3] = {0, 1, 2};
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j)
+                if (cm[perm[j]] > cm[perm[i]]) {
+                    int tt = perm[i];
+                    perm[i] = perm[j];
+                    perm[j] = tt;
+                }
+        uint32_t total = 0;
+        for (int p = 0; p < 3; ++p) {
+            plan->perm[p] = perm[p];
+            plan->bits[p] = bitlen(cm[perm[p]]);
+            total += plan->bits[p];
+        }
+        s_perm0 = perm[0];
+        if (total > 61) {
+            plan->status |= ST_KEY_OVERFLOW;
+            plan->sort.n = 0;
+            s_stop = 1;
+            publish();
+        } else {
+            plan->key_bits = total + 3;
+            plan->use_cols =
+                (prm.nf == 1 && plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
+            plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
+            plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (s_stop) return;
+    // each frame's slab entries (the brick rows of its major cell
+    // coordinates), laid out in frame order: an exclusive scan in chunks of
+    // 256 frames
+    const int p0 = s_perm0;
+    CellKeyLayout L;
+    L.load(plan);
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < prm.nf; c0 += blockDim.x) {
+        const uint32_t f = c0 + t;
+        uint32_t ns = 0;
+        if (f < prm.nf)
+            ns = (uint32_t)L.slab_of(
+                     (unsigned long long)(((int64_t)__ldcg(&fr[f].hi[p0]) - __ldcg(&fr[f].lo[p0])) / prm.S)) + 1u;
+        s_scan[t] = ns;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+            const uint32_t v = t >= o ? s_scan[t - o] : 0u;
+            __syncthreads();
+            s_scan[t] += v;
+            __syncthreads();
+        }
+        if (f < prm.nf) {
+            fr[f].nslab = ns;
+            fr[f].slab_base = carry + s_scan[t] - ns;
+        }
+        carry += s_scan[255];
+        __syncthreads();
+    }
+    if (t == 0) {
+        plan->slab_need = carry;
+        if (carry > prm.slab_cap) {  // the host grows the slab index and runs the call again
+            plan->status |= ST_SIZE_OVERFLOW;
+            plan->sort.n = 0;
+        }
+        publish();
+    }
+}
+
 // a1: validate and quantise every coordinate, reduce each frame's bounding
 // box of q.  A block keeps its partial box until one of its units belongs
-// to another frame (a single cloud: once, at the end).
+// to another frame (a single cloud: once, at the end).  The last block to
+// finish then runs plan_body.
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, Plan *plan,
                                               Frame *__restrict__ fr, Params prm)
@@ -253,108 +352,18 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ xyz, Pla
     if (cur != 0xffffffffu) flush();
     if (st) atomicOr(&s_st, st);
     __syncthreads();
-    if (threadIdx.x == 0 && s_st) atomicOr(&plan->status, s_st);
-}
-
-// a1: choose the axis order (largest cell extent major, smallest minor) and
-// the key layout, the same for every frame of the call (from the largest
-// extent per axis over the frames); lay out each frame's part of the slab
-// index; disable the rest of the pipeline on a data error.  One block.
-__global__ void __launch_bounds__(256) k_plan(Plan *plan, Frame *__restrict__ fr, Params prm)
-{
-    grid_enter();
-    __shared__ uint32_t s_cm[3];
-    __shared__ uint32_t s_scan[256];
-    __shared__ int s_perm0;
-    __shared__ uint32_t s_stop;
-    const int t = threadIdx.x;
-    if (t < 3) s_cm[t] = 0;
-    if (t == 0) s_stop = (plan->status & (ST_NONFINITE | ST_OUT_OF_RANGE)) ? 1u : 0u;
-    __syncthreads();
-    // the host's 16-byte read-back of the outcome
-    auto publish = [&]() {
-        plan->front[0] = plan->status;
-        plan->front[1] = plan->sort.key64;
-        plan->front[2] = plan->sort.npasses;
-        plan->front[3] = plan->key_bits;
-    };
-    if (s_stop) {
-        if (t == 0) {
-            plan->sort.n = 0;
-            publish();
-        }
-        return;
-    }
-    for (uint32_t f = t; f < prm.nf; f += blockDim.x)
-        for (int a = 0; a < 3; ++a)
-            atomicMax(&s_cm[a], (uint32_t)(((int64_t)fr[f].hi[a] - fr[f].lo[a]) / prm.S));
-    __syncthreads();
-    if (t == 0) {
-        uint32_t cm[3] = {s_cm[0], s_cm[1], s_cm[2]};
-        int perm[3] = {0, 1, 2};
-        for (int i = 0; i < 3; ++i)
-            for (int j = i + 1; j < 3; ++j)
-                if (cm[perm[j]] > cm[perm[i]]) {
-                    int tt = perm[i];
-                    perm[i] = perm[j];
-                    perm[j] = tt;
-                }
-        uint32_t total = 0;
-        for (int p = 0; p < 3; ++p) {
-            plan->perm[p] = perm[p];
-            plan->bits[p] = bitlen(cm[perm[p]]);
-            total += plan->bits[p];
-        }
-        s_perm0 = perm[0];
-        if (total > 61) {
-            plan->status |= ST_KEY_OVERFLOW;
-            plan->sort.n = 0;
-            s_stop = 1;
-            publish();
-        } else {
-            plan->key_bits = total + 3;
-            plan->use_cols =
-                (prm.nf == 1 && plan->bits[0] + plan->bits[1] <= prm.col_bits) ? 1u : 0u;
-            plan->sort.npasses = (total + 3 + kRadixBits - 1) / kRadixBits;
-            plan->sort.key64 = (total + 3) > 32 ? 1u : 0u;
-        }
+    // the last block to finish lays out the plan (every block's boxes and
+    // status bits are in memory before it counts itself done)
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        if (s_st) atomicOr(&plan->status, s_st);
+        __threadfence();
+        s_last = atomicAdd(&plan->bbox_done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (s_stop) return;
-    // each frame's slab entries (the brick rows of its major cell
-    // coordinates), laid out in frame order: an exclusive scan in chunks of
-    // 256 frames
-    const int p0 = s_perm0;
-    CellKeyLayout L;
-    L.load(plan);
-    uint32_t carry = 0;
-    for (uint32_t c0 = 0; c0 < prm.nf; c0 += blockDim.x) {
-        const uint32_t f = c0 + t;
-        uint32_t ns = 0;
-        if (f < prm.nf)
-            ns = (uint32_t)L.slab_of((unsigned long long)(((int64_t)fr[f].hi[p0] - fr[f].lo[p0]) / prm.S)) + 1u;
-        s_scan[t] = ns;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-            const uint32_t v = t >= o ? s_scan[t - o] : 0u;
-            __syncthreads();
-            s_scan[t] += v;
-            __syncthreads();
-        }
-        if (f < prm.nf) {
-            fr[f].nslab = ns;
-            fr[f].slab_base = carry + s_scan[t] - ns;
-        }
-        carry += s_scan[255];
-        __syncthreads();
-    }
-    if (t == 0) {
-        plan->slab_need = carry;
-        if (carry > prm.slab_cap) {  // the host grows the slab index and runs the call again
-            plan->status |= ST_SIZE_OVERFLOW;
-            plan->sort.n = 0;
-        }
-        publish();
+    if (s_last) {
+        __threadfence();
+        plan_body(plan, fr, prm);
     }
 }
 
@@ -814,17 +823,67 @@ __device__ __forceinline__ float centre_dist2(const Rec &r, const int32_t org[3]
     return dx * dx + dy * dy + dz * dz;
 }
 
+// a3: slab index over the brick rows of the major cell coordinate (see
+// CellKeyLayout): cells of slab x occupy [slab_lo[x], slab_hi[x]) of the
+// sorted cell array (empty: lo == hi == 0); and, when it fits, the dense
+// column index over (c_p0, c_p1) (the cell key above c_p2) the same way.
+// One thread per cell; run by the sub-cell statistics kernel after its own
+// loop (the two read only the cell table).
+__device__ __forceinline__ void slab_index(const Plan *plan, const unsigned long long *__restrict__ cell_key,
+                                           const uint32_t *__restrict__ cell_sc,
+                                           const uint8_t *__restrict__ scode,
+                                           uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
+                                           uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
+                                           uint8_t *__restrict__ cocc, const uint32_t *__restrict__ cframe,
+                                           const Frame *__restrict__ fr, uint32_t nf)
+{
+    const uint32_t M = plan->M_c;
+    CellKeyLayout L;
+    L.load(plan);
+    const uint32_t b2 = L.b2;
+    const uint32_t sh = L.b2 + L.b1 + L.B0;  // key bits below the brick row
+    const bool cols = plan->use_cols != 0;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        const unsigned long long k = cell_key[c];
+        const unsigned long long x = k >> sh, col = k >> b2;
+        const unsigned long long kp = c > 0 ? cell_key[c - 1] : ~0ull;
+        const unsigned long long kn = c + 1 < M ? cell_key[c + 1] : ~0ull;
+        // slab x of the cell's frame; a frame change also ends a slab
+        const uint32_t f = nf > 1 ? cframe[c] : 0u;
+        const bool fprev = nf > 1 && c > 0 && cframe[c - 1] != f;
+        const bool fnext = nf > 1 && c + 1 < M && cframe[c + 1] != f;
+        const uint32_t se = fr[f].slab_base + (uint32_t)x;
+        if (c == 0 || fprev || (kp >> sh) != x) slab_lo[se] = c;
+        if (c + 1 == M || fnext || (kn >> sh) != x) slab_hi[se] = c + 1;
+        if (cols) {
+            if (c == 0 || (kp >> b2) != col) col_lo[col] = c;
+            if (c + 1 == M || (kn >> b2) != col) col_hi[col] = c + 1;
+        }
+        // occupancy of the cell: bit s set when sub-cell code s is present
+        // (its sub-cells are stored in increasing code order)
+        uint32_t occ = 0;
+        const uint32_t e = min(cell_sc[c + 1], cell_sc[c] + 8u);
+        for (uint32_t a = cell_sc[c]; a < e; ++a) occ |= 1u << (scode[a] & 7u);
+        cocc[c] = (uint8_t)occ;
+    }
+}
+
 // a3: per sub-cell box, count, smallest original index and representative
 // (the point nearest the sub-cell's nominal centre), in one pass over its
 // points; initialise the union-find and component arrays.  Sub-cells above
-// kBigSubcell points are queued for k_subcell_big.
+// prm.big_subcell points are queued for k_subcell_large.  Then the slab and
+// column index and the cell occupancies (slab_index).
 __global__ void __launch_bounds__(256)
     k_subcell_stats(Plan *plan, Params prm, const Rec *__restrict__ rec,
                     const uint32_t *__restrict__ sc_start, SubBox *__restrict__ box,
                     uint32_t *__restrict__ sminidx, uint32_t *__restrict__ parent,
                     uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
                     int32_t *__restrict__ crank, uint32_t *__restrict__ big, uint32_t *__restrict__ reps,
-                    const Frame *__restrict__ fr)
+                    const Frame *__restrict__ fr, const unsigned long long *__restrict__ cell_key,
+                    const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
+                    uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
+                    uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
+                    uint8_t *__restrict__ cocc, const uint32_t *__restrict__ cframe)
 {
     grid_enter();
     if (call_aborted(&plan->status)) return;
@@ -886,6 +945,7 @@ __global__ void __launch_bounds__(256)
         sminidx[a] = mi;
         reps[a] = pack_rep(rp, b.lx, b.ly, b.lz);
     }
+    slab_index(plan, cell_key, cell_sc, scode, slab_lo, slab_hi, col_lo, col_hi, cocc, cframe, fr, prm.nf);
 }
 
 // a3: the same for the queued sub-cells of big_subcell..kHugeSubcell points,
@@ -1043,51 +1103,6 @@ __global__ void __launch_bounds__(256)
                     gridDim.x - huge_blocks);
 }
 
-// a3: slab index over the brick rows of the major cell coordinate (see
-// CellKeyLayout): cells of slab x occupy [slab_lo[x], slab_hi[x]) of the
-// sorted cell array (empty: lo == hi == 0); and, when it fits, the dense
-// column index over (c_p0, c_p1) (the cell key above c_p2) the same way.
-__global__ void __launch_bounds__(256)
-    k_slabs(Plan *plan, const unsigned long long *__restrict__ cell_key,
-            const uint32_t *__restrict__ cell_sc, const uint8_t *__restrict__ scode,
-            uint32_t *__restrict__ slab_lo, uint32_t *__restrict__ slab_hi,
-            uint32_t *__restrict__ col_lo, uint32_t *__restrict__ col_hi,
-            uint8_t *__restrict__ cocc, const uint32_t *__restrict__ cframe,
-            const Frame *__restrict__ fr, uint32_t nf)
-{
-    grid_enter();
-    if (call_aborted(&plan->status)) return;
-    const uint32_t M = plan->M_c;
-    CellKeyLayout L;
-    L.load(plan);
-    const uint32_t b2 = L.b2;
-    const uint32_t sh = L.b2 + L.b1 + L.B0;  // key bits below the brick row
-    const bool cols = plan->use_cols != 0;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
-        const unsigned long long k = cell_key[c];
-        const unsigned long long x = k >> sh, col = k >> b2;
-        const unsigned long long kp = c > 0 ? cell_key[c - 1] : ~0ull;
-        const unsigned long long kn = c + 1 < M ? cell_key[c + 1] : ~0ull;
-        // slab x of the cell's frame; a frame change also ends a slab
-        const uint32_t f = nf > 1 ? cframe[c] : 0u;
-        const bool fprev = nf > 1 && c > 0 && cframe[c - 1] != f;
-        const bool fnext = nf > 1 && c + 1 < M && cframe[c + 1] != f;
-        const uint32_t se = fr[f].slab_base + (uint32_t)x;
-        if (c == 0 || fprev || (kp >> sh) != x) slab_lo[se] = c;
-        if (c + 1 == M || fnext || (kn >> sh) != x) slab_hi[se] = c + 1;
-        if (cols) {
-            if (c == 0 || (kp >> b2) != col) col_lo[col] = c;
-            if (c + 1 == M || (kn >> b2) != col) col_hi[col] = c + 1;
-        }
-        // occupancy of the cell: bit s set when sub-cell code s is present
-        // (its sub-cells are stored in increasing code order)
-        uint32_t occ = 0;
-        const uint32_t e = min(cell_sc[c + 1], cell_sc[c] + 8u);
-        for (uint32_t a = cell_sc[c]; a < e; ++a) occ |= 1u << (scode[a] & 7u);
-        cocc[c] = (uint8_t)occ;
-    }
-}
-
 cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, const FrontArgs &fa,
                           cudaStream_t st)
 {
@@ -1106,8 +1121,6 @@ cudaError_t enqueue_front(Workspace &ws, const float *xyz, const Params &prm, co
     if (multi) launch(k_bbox<true>, grid, 256, 0, st, xyz, ws.plan, ws.frames, prm);
     else launch(k_bbox<false>, grid, 256, 0, st, xyz, ws.plan, ws.frames, prm);
     FEC_MARK(ws, "k_bbox", st);
-    launch(k_plan, 1, 256, 0, st, ws.plan, ws.frames, prm);
-    FEC_MARK(ws, "k_plan", st);
     Clears clr;
     clr.sort_status = ws.sort_status;
     clr.sort_words = ((size_t)prm.ntiles + 1) * kRadixBins;  // look-back array 0, this call's tiles
@@ -1160,8 +1173,8 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
 #undef FEC_CELLS_ARGS
     FEC_MARK(ws, "k_cells", st);
     launch(k_subcell_stats, grid1, 256, 0, st, ws.plan, prm, ws.rec, ws.sc_start, ws.box, ws.sminidx,
-                                           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps,
-                                           ws.frames);
+           ws.parent, ws.csize, ws.cmin, ws.crank, ws.big, ws.reps, ws.frames, ws.cell_key, ws.cell_sc,
+           ws.scode, ws.slab_lo, ws.slab_hi, ws.col_lo, ws.col_hi, ws.cocc, ws.cframe);
     FEC_MARK(ws, "k_subcell_stats", st);
     const int huge_blocks = grid_for(ws, prm.n / (kHugeSubcell + 1), 1, 2);
     const int big_blocks = grid_for(ws, prm.n / (prm.big_subcell + 1), 8, 4);
@@ -1169,9 +1182,6 @@ cudaError_t enqueue_cells(Workspace &ws, const float *xyz, const Params &prm, cu
                                                              ws.box, ws.sminidx, ws.reps, ws.frames,
                                                              (uint32_t)huge_blocks);
     FEC_MARK(ws, "k_subcell_large", st);
-    launch(k_slabs, grid1, 256, 0, st, ws.plan, ws.cell_key, ws.cell_sc, ws.scode, ws.slab_lo, ws.slab_hi,
-                                  ws.col_lo, ws.col_hi, ws.cocc, ws.cframe, ws.frames, prm.nf);
-    FEC_MARK(ws, "k_slabs", st);
     return cudaGetLastError();
 }
 

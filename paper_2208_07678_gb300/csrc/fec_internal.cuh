@@ -4,10 +4,10 @@
 // The pipeline for one cloud (Eq. 1 as connected components; Algorithm 1's
 // input/output) runs without host round trips until the final read-back:
 //
-//   a1  quantise + bounding box + validation            k_bbox, k_plan
+//   a1  quantise + bounding box + validation, plan      k_bbox (its last block: plan_body)
 //   a1  grid keys (cell of side S=2h, sub-cell bits)    k_keys (+ radix digit histograms)
 //   a2  LSD radix sort of (key, index), onesweep        k_onesweep (per 8-bit digit)
-//   a3  cell table: sub-cell/cell heads, scan, gather   k_cells, k_subcell_stats, k_slabs
+//   a3  cell table: sub-cell/cell heads, scan, gather   k_cells, k_subcell_stats (+ slab index)
 //   a4  neighbour lists, neighbour test + union         k_nbrs, k_region, k_edges, k_pairs
 //       (27-cell stencil, region-local union-find)
 //   a5  flatten + component statistics                  k_flatten_stats
@@ -164,9 +164,9 @@ __device__ __forceinline__ uint32_t frame_of_tile(const Frame *fr, uint32_t nf, 
     return nf > 1 ? frame_search(fr, nf, t, 2) : 0u;
 }
 
-// Per-call plan (device memory), written by k_plan / k_cells / kernels.
+// Per-call plan (device memory), written by plan_body / k_cells / kernels.
 struct Plan {
-    // written by k_plan for the host: status, key64, passes of the main
+    // written by plan_body for the host: status, key64, passes of the main
     // sort, key bits (one 16-byte read-back decides which sort passes to
     // launch)
     uint32_t front[4];
@@ -184,9 +184,12 @@ struct Plan {
     uint32_t region_counter;    // dynamic regions of the neighbour step
     uint32_t slab_need;         // slab-index entries the frames need (all frames)
     uint32_t rank_tile_counter; // dynamic tiles of the kept-component ranking scan
+    uint32_t bbox_done;         // blocks of k_bbox finished (the last one lays out the plan)
+    uint32_t kept_n;            // kept components
     unsigned long long ctr[8];  // work counters of the union step (CTR_*)
+    // Everything above is the call's summary, read back by the host in one
+    // copy of offsetof(Plan, sort) bytes after the call's last kernel.
     SortCtl sort;              // main (key, index) sort
-    SortCtl kept;              // kept components: kept.n is their count
 };
 
 // Host-side constants of one call, passed by value.

@@ -133,7 +133,7 @@ extern "C" fec_status fec_cluster_noalloc(const float *xyz, int64_t n, float d, 
         e = cudaMemcpyAsync(&status_bits, &ws.plan->status, sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&k, &ws.plan->kept.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(&k, &ws.plan->kept_n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(256)
         if (!mask) continue;
         const int leader = __ffs(mask) - 1;
         uint32_t slot = 0;
-        if (lane == leader) slot = atomicAdd(&plan->kept.n, (uint32_t)__popc(mask));
+        if (lane == leader) slot = atomicAdd(&plan->kept_n, (uint32_t)__popc(mask));
         slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(mask & lanemask_lt());
         if (keep && FEC_IN_BOUNDS(&plan->status, slot, M)) {
             kept_key[slot] = pos;
@@ -1114,7 +1114,7 @@ __global__ void __launch_bounds__(256)
 {
     grid_enter();
     if (call_aborted(&plan->status)) return;
-    const uint32_t k = plan->kept.n;
+    const uint32_t k = plan->kept_n;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) {
         const uint32_t pos = kept_key[t];
         if (!FEC_IN_BOUNDS(&plan->status, pos, plan->sort.n) ||
