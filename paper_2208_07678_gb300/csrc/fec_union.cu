@@ -395,8 +395,9 @@ constexpr int kRegionSubs = 8 * kRegionCells;
 static_assert(kRegionSubs <= 65536, "region-local sub-cell indices are 16-bit");
 constexpr int kRegionBuf = 512;
 
+using RegionPar = uint16_t;
 struct RegionSmem {
-    uint16_t par[kRegionSubs];             // union-find parent, region-local (< 2^16)
+    RegionPar par[kRegionSubs];            // union-find parent, region-local (< 2^16)
     uint2 ebuf[kRegionBuf];   // boundary edges
     uint2 qbuf[kRegionBuf];   // cross-region undecided pairs
     uint32_t ecount, qcount, next, region, rend, pad[3];
@@ -410,7 +411,7 @@ struct RegionSmem {
     uint32_t qb[kRegionWarps][64];
 };
 
-__device__ __forceinline__ uint32_t s_find(volatile uint16_t *par, uint32_t x)
+__device__ __forceinline__ uint32_t s_find(volatile RegionPar *par, uint32_t x)
 {
     for (;;) {
         const uint32_t p = par[x];
@@ -422,9 +423,9 @@ __device__ __forceinline__ uint32_t s_find(volatile uint16_t *par, uint32_t x)
     }
 }
 
-__device__ __forceinline__ void s_unite(uint16_t *par, uint32_t a, uint32_t b)
+__device__ __forceinline__ void s_unite(RegionPar *par, uint32_t a, uint32_t b)
 {
-    volatile uint16_t *vp = par;
+    volatile RegionPar *vp = par;
     for (;;) {
         a = s_find(vp, a);
         b = s_find(vp, b);
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
     m.R1 = prm.R + 1;
     uint32_t n_pairs = 0, n_yes = 0, n_und = 0, n_same = 0, n_queued = 0, n_edges = 0;
     unsigned long long n_evals = 0;
-    volatile uint16_t *vpar = S.par;
+    volatile RegionPar *vpar = S.par;
     // this block's list of undecided in-region pairs (local indices a | b << 16
     // would not fit 8192 sub-cells twice, so two u16 halves of a u32: a, b < 8192)
     uint32_t *const my_scratch = scratch + (size_t)blockIdx.x * scap;
@@ -543,6 +544,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
         // another), drops those that no point pair can join, and queues the
         // rest in shared memory; every 32 queued pairs are decided together.
         uint32_t qn = 0;                  // pairs in the warp's queue
+        uint32_t qh = 0;                  // its first entry (a ring of 64)
         // Each half-warp (16 lanes) enumerates one cell, so that the two
         // cells' set-up loads are in flight together.
         const int hw = lane >> 4, hl = lane & 15;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 }
                 const uint32_t pm = __ballot_sync(0xffffffffu, possible);
                 if (possible) {
-                    const uint32_t slot = qn + __popc(pm & lanemask_lt());
+                    const uint32_t slot = (qh + qn + __popc(pm & lanemask_lt())) & 63u;
                     S.qa[w][slot] = a;
                     S.qb[w][slot] = b;
                 }
@@ -643,36 +645,31 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
             uint32_t a = 0, b = 0;
             int dec = 0;
             bool local = true;
-            if ((uint32_t)lane < mq && FEC_IN_BOUNDS(status, S.qa[w][lane] - s0, ns) &&
-                FEC_IN_BOUNDS(status, S.qb[w][lane], Ms)) {
-                a = S.qa[w][lane];
-                b = S.qb[w][lane];
+            uint32_t root_a = 0, root_b = 0;  // local pairs: their roots at the check
+            const uint32_t qs = (qh + lane) & 63u;
+            if ((uint32_t)lane < mq && FEC_IN_BOUNDS(status, S.qa[w][qs] - s0, ns) &&
+                FEC_IN_BOUNDS(status, S.qb[w][qs], Ms)) {
+                a = S.qa[w][qs];
+                b = S.qb[w][qs];
                 local = b - s0 < ns;
                 const SubBox BA = box[a], BB = box[b];
                 const uint32_t RA = reps[a], RB = reps[b];
-                if (local && s_find(vpar, a - s0) == s_find(vpar, b - s0)) {
+                if (local) {
+                    root_a = s_find(vpar, a - s0);
+                    root_b = s_find(vpar, b - s0);
+                }
+                if (local && root_a == root_b) {
                     ++n_same;
                 } else {
                     ++n_pairs;
                     dec = box_decide<WIDE>(BA, BB, RA, RB, m);
                 }
             }
-            // the rest of the queue (fewer than 32) moves to its front
-            uint32_t ra = 0, rb = 0;
-            const bool rest = (uint32_t)lane + 32 < qn;
-            if (rest) {
-                ra = S.qa[w][lane + 32];
-                rb = S.qb[w][lane + 32];
-            }
-            __syncwarp();
-            if (rest) {
-                S.qa[w][lane] = ra;
-                S.qb[w][lane] = rb;
-            }
+            qh = (qh + mq) & 63u;  // the queue is a ring: the rest stays in place
             qn -= mq;
             if (dec == 1 && local) {
                 ++n_yes;
-                s_unite(S.par, a - s0, b - s0);
+                s_unite(S.par, root_a, root_b);  // from the roots found at the check
             }
             const bool emit = dec == 1 && !local;
             n_edges += emit ? 1 : 0;
@@ -705,9 +702,10 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                 smask &= smask - 1;
                 const uint32_t pa = __shfl_sync(0xffffffffu, a, src) - s0;
                 const uint32_t pb = __shfl_sync(0xffffffffu, b, src) - s0;
-                if (s_find(vpar, pa) == s_find(vpar, pb)) continue;  // warp-uniform
+                const uint32_t fa = s_find(vpar, pa), fb = s_find(vpar, pb);
+                if (fa == fb) continue;  // warp-uniform
                 if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
-                    s_unite(S.par, pa, pb);
+                    s_unite(S.par, fa, fb);
                 __syncwarp();
             }
             __syncwarp();
@@ -735,9 +733,10 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
                     const uint32_t pa = __shfl_sync(0xffffffffu, la, src);
                     const uint32_t pb = __shfl_sync(0xffffffffu, lb, src);
                     // warp-uniform: every lane reads the same shared words
-                    if (s_find(vpar, pa) == s_find(vpar, pb)) continue;
+                    const uint32_t fa = s_find(vpar, pa), fb = s_find(vpar, pb);
+                    if (fa == fb) continue;
                     if (warp_pair_test<WIDE>(s0 + pa, s0 + pb, box, rec, m, n_evals) && lane == 0)
-                        s_unite(S.par, pa, pb);
+                        s_unite(S.par, fa, fb);
                     __syncwarp();
                 }
             }
