@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(kUnionThreads, 2)
 constexpr int kFlatSlots = 512;  // per-block table of component sums
 
 __global__ void __launch_bounds__(256, 4)
-    k_flatten_stats(Plan *plan, const SubBox *__restrict__ box, const uint32_t *__restrict__ sminidx,
+    k_flatten_stats(Plan *plan, const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ sminidx,
                     uint32_t *parent, uint32_t *__restrict__ csize, uint32_t *__restrict__ cmin,
                     uint32_t union_cap)
 {
@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(256, 4)
                 r = p;
             }
             if (!found) atomicOr(&plan->status, ST_UNION_CAP);
-            cnt = box[a].count;
+            cnt = sc_start[a + 1] - sc_start[a];  // the sub-cell's points (not its 32-byte box)
             mi = sminidx[a];
             st_relaxed(parent + a, r);
         }
@@ -1248,7 +1248,7 @@ cudaError_t enqueue_union(Workspace &ws, const Params &prm, cudaStream_t st)
         launch(k_pairs<true>, grid_for(ws, prm.n, 64, 2), kUnionThreads, 0, st, ws.plan, prm, ws.box, ws.rec, ws.parent,
                                                             ws.pairq, qcap);
     FEC_MARK(ws, "k_pairs", st);
-    launch(k_flatten_stats, grid1, 256, 0, st, ws.plan, ws.box, ws.sminidx, ws.parent, ws.csize,
+    launch(k_flatten_stats, grid1, 256, 0, st, ws.plan, ws.sc_start, ws.sminidx, ws.parent, ws.csize,
                                                  ws.cmin, prm.union_cap);
     FEC_MARK(ws, "k_flatten_stats", st);
     launch(k_kept, grid1, 256, 0, st, ws.plan, ws.parent, ws.csize, ws.cmin, ws.frames, prm.nf,
