@@ -89,10 +89,10 @@ constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept pe
 #define FEC_REGION_CELLS 1024
 #endif
 #ifndef FEC_REGION_THREADS
-#define FEC_REGION_THREADS 256
+#define FEC_REGION_THREADS 512
 #endif
 #ifndef FEC_REGION_BLOCKS
-#define FEC_REGION_BLOCKS 4
+#define FEC_REGION_BLOCKS 2
 #endif
 constexpr uint32_t kRegionCellsPerBlock = FEC_REGION_CELLS;
 constexpr int kRegionThreads = FEC_REGION_THREADS;
