@@ -393,7 +393,10 @@ constexpr int kRegionCells = (int)kRegionCellsPerBlock;
 constexpr int kRegionWarps = kRegionThreads / 32;
 constexpr int kRegionSubs = 8 * kRegionCells;
 static_assert(kRegionSubs <= 65536, "region-local sub-cell indices are 16-bit");
-constexpr int kRegionBuf = 512;
+#ifndef FEC_REGION_BUF
+#define FEC_REGION_BUF 1024
+#endif
+constexpr int kRegionBuf = FEC_REGION_BUF;
 
 using RegionPar = uint16_t;
 struct RegionSmem {
