@@ -694,6 +694,38 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             }
             if (lane == 0) s_prefix = prefix;
         }
+        // The sorted records do not depend on the prefix: staged here, the
+        // other warps build them while warp 0 looks back.
+        {
+            uint32_t fr_i = f0;
+#pragma unroll
+            for (int i = 0; i < kScanIPT; ++i) {
+                const uint32_t p = p0 + i;
+                if (p >= n) break;
+                if (i > 0 && ((fstarts >> i) & 1u)) ++fr_i;
+                if (MULTI && PACKED && fr_i != gframe) {  // the grid origin of the position's frame
+                    g.set_frame(fr[fr_i]);
+                    gframe = fr_i;
+                }
+                const uint32_t idx = (uint32_t)vv[i];
+                Rec r;
+                if (PACKED) {
+                    int32_t q[3];
+                    g.unpack<KeyT>(k[i], (unsigned long long)vv[i], q);
+                    r.x = q[0];
+                    r.y = q[1];
+                    r.z = q[2];
+                } else if (idx < prm.rows) {  // gather from the input (cells wider than 1024 units)
+                    quantize1(xyz[3 * (size_t)idx + 0], r.x);
+                    quantize1(xyz[3 * (size_t)idx + 1], r.y);
+                    quantize1(xyz[3 * (size_t)idx + 2], r.z);
+                } else {  // only after a look-back timeout (reported below)
+                    r.x = r.y = r.z = 0;
+                }
+                r.idx = idx;
+                s_rec[tid * kScanIPT + i] = r;
+            }
+        }
         __syncthreads();
         const unsigned long long base = s_prefix + s_warp[warp] + (incl - run);
 
@@ -704,10 +736,6 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
             const uint32_t p = p0 + i;
             if (p >= n) break;
             if (i > 0 && ((fstarts >> i) & 1u)) ++fcur;
-            if (MULTI && PACKED && fcur != gframe) {  // the grid origin of the position's frame
-                g.set_frame(fr[fcur]);
-                gframe = fcur;
-            }
             const unsigned long long cur = base + flag[i];
             const uint32_t sc = (uint32_t)(cur & 0x7fffffffull) - 1u;
             const uint32_t c = (uint32_t)(cur >> 31) - 1u;
@@ -729,20 +757,6 @@ __device__ __forceinline__ void cells_body(Plan *plan, const Params &prm, const 
                 cell_sc[c] = sc;
                 if (MULTI) cframe[c] = fcur;
             }
-            Rec r;
-            if (PACKED) {
-                int32_t q[3];
-                g.unpack<KeyT>(k[i], (unsigned long long)vv[i], q);
-                r.x = q[0];
-                r.y = q[1];
-                r.z = q[2];
-            } else {  // gather from the input (cells wider than 1024 units)
-                quantize1(xyz[3 * (size_t)idx + 0], r.x);
-                quantize1(xyz[3 * (size_t)idx + 1], r.y);
-                quantize1(xyz[3 * (size_t)idx + 2], r.z);
-            }
-            r.idx = idx;
-            s_rec[tid * kScanIPT + i] = r;
             if (p == n - 1) {
                 plan->M_s = sc + 1;
                 plan->M_c = c + 1;
