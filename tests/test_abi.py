@@ -98,3 +98,13 @@ def test_product_path_does_not_import_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "fec_oracle" not in src, f
+
+
+def test_library_selection_by_environment(monkeypatch):
+    """FEC_LIBRARY=debug selects the bounds-checked build; anything else the release one."""
+    monkeypatch.setenv("FEC_LIBRARY", "debug")
+    assert fec.debug_library() and fec.library_path() == libbuild.LIB_DEBUG
+    monkeypatch.setenv("FEC_LIBRARY", "release")
+    assert not fec.debug_library() and fec.library_path() == libbuild.LIB
+    monkeypatch.delenv("FEC_LIBRARY")
+    assert fec.library_path() == libbuild.LIB
