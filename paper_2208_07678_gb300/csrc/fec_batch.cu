@@ -5,7 +5,7 @@
 // pipeline over all of its frames: the frame table (see Frame) makes the sort
 // segmented by frame, the cell table start a new cell at every frame, the
 // size bounds and the numbering per frame, so a group of a hundred frames
-// takes the same ~35 launches as one cloud, with every kernel persistent over
+// takes the same ~20 launches as one cloud, with every kernel persistent over
 // all the group's points.  Groups run concurrently on up to 8 lanes (a CUDA
 // stream and a workspace each), and the whole fork/join sequence -- the
 // labels' -1 fill, the frame tables' uploads, every group's pipeline and the
@@ -16,11 +16,12 @@
 // Autotuner: the first time a batch shape is seen, the launch configuration
 // is tuned on it by coordinate descent, each candidate captured and timed with
 // CUDA events: the number of lanes (how many groups run at once), the largest
-// region of the neighbour step (cells per block, 256 / 512 / 1024) and the
-// sub-cell size above which a warp instead of a thread reduces a sub-cell
-// (points per warp, 32 / 64 / 128).  The winner is kept in memory and in the
-// context's tuning file when one was given (one "key lanes region big" line
-// per shape).
+// region of the neighbour step (cells per block, 256 / 512 / 1024), the
+// schedule of that step (its last grid-full of regions cut 1, 2 or 4 times
+// smaller, so that the blocks finish together) and the sub-cell size above
+// which a warp instead of a thread reduces a sub-cell (points per warp, 32 /
+// 64 / 128).  The winner is kept in memory and in the context's tuning file
+// when one was given (one "key lanes region big tail" line per shape).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -74,6 +75,7 @@ struct Config {
     int lanes = 1;
     uint32_t region = kRegionCellsPerBlock;
     uint32_t big = kBigSubcell;
+    uint32_t tail = kRegionTailDiv;
 };
 
 // Frames of one radius, run as one pipeline call.
@@ -322,7 +324,7 @@ std::string shape_key(const int64_t *offsets, int32_t nb, const float *d, const 
     mix(&xyz, sizeof(xyz));
     mix(&labels, sizeof(labels));
     char buf[96];
-    std::snprintf(buf, sizeof(buf), "%016llx/%d/%d/%u/%u", h, nb, c.lanes, c.region, c.big);
+    std::snprintf(buf, sizeof(buf), "%016llx/%d/%d/%u/%u/%u", h, nb, c.lanes, c.region, c.big, c.tail);
     return buf;
 }
 
@@ -348,15 +350,19 @@ void load_tuning(BatchEngine &e)
     if (e.tune_path.empty()) return;
     FILE *f = std::fopen(e.tune_path.c_str(), "r");
     if (!f) return;
-    char key[128];
-    Config c;
-    unsigned region = 0, big = 0;
-    while (std::fscanf(f, "%127s %d %u %u", key, &c.lanes, &region, &big) == 4) {
-        if (c.lanes < 1 || c.lanes > kMaxLanes || region < kRegionMinCells ||
-            region > kRegionCellsPerBlock || big < 1 || big > (unsigned)kHugeSubcell)
+    char line[256], key[128];
+    while (std::fgets(line, sizeof(line), f)) {
+        // "key lanes region big [tail]" (files without the tail use the default)
+        Config c;
+        unsigned region = 0, big = 0, tail = kRegionTailDiv;
+        const int got = std::sscanf(line, "%127s %d %u %u %u", key, &c.lanes, &region, &big, &tail);
+        if (got < 4 || c.lanes < 1 || c.lanes > kMaxLanes || region < kRegionMinCells ||
+            region > kRegionCellsPerBlock || big < 1 || big > (unsigned)kHugeSubcell || tail < 1 ||
+            tail > 8)
             continue;
         c.region = region;
         c.big = big;
+        c.tail = tail;
         e.tuned[key] = c;
     }
     std::fclose(f);
@@ -368,8 +374,8 @@ void save_tuning(const BatchEngine &e)
     FILE *f = std::fopen(e.tune_path.c_str(), "w");
     if (!f) return;
     for (const auto &kv : e.tuned)
-        std::fprintf(f, "%s %d %u %u\n", kv.first.c_str(), kv.second.lanes, kv.second.region,
-                     kv.second.big);
+        std::fprintf(f, "%s %d %u %u %u\n", kv.first.c_str(), kv.second.lanes, kv.second.region,
+                     kv.second.big, kv.second.tail);
     std::fclose(f);
 }
 
@@ -446,6 +452,7 @@ fec_status capture(BatchEngine &e, const Config &c, const std::vector<Group> &gr
             prm.slab_cap = e.slab_cap;
             prm.region_cells = c.region;
             prm.big_subcell = c.big;
+            prm.region_tail = c.tail;
             FrontArgs fa;
             fa.single = false;
             err = enqueue_cluster(ln.ws, xyz, prm, fa, labels, false, ln.st);
@@ -515,7 +522,8 @@ fec_status time_config(BatchEngine &e, cudaStream_t main, const Config &c, size_
     return FEC_OK;
 }
 
-// Coordinate descent over lanes, then region size, then the warp threshold.
+// Coordinate descent over lanes, then region size, then the region schedule,
+// then the warp threshold.
 fec_status autotune(BatchEngine &e, cudaStream_t main, size_t budget, const float *xyz,
                     const int64_t *offsets, int32_t nb, const float *d, const int64_t *mn,
                     const int64_t *mx, int32_t *labels, Config *out)
@@ -546,6 +554,14 @@ fec_status autotune(BatchEngine &e, cudaStream_t main, size_t budget, const floa
         if (r == base_r.region) continue;
         Config c = base_r;
         c.region = r;
+        const fec_status s = consider(c);
+        if (s != FEC_OK) return s;
+    }
+    const Config base_t = best;
+    for (uint32_t t : {1u, 2u, 4u}) {
+        if (t == base_t.tail) continue;
+        Config c = base_t;
+        c.tail = t;
         const fec_status s = consider(c);
         if (s != FEC_OK) return s;
     }

@@ -95,6 +95,10 @@ constexpr uint32_t kRegionScratch = 32768;  // undecided in-region pairs kept pe
 #define FEC_REGION_BLOCKS 2
 #endif
 constexpr uint32_t kRegionCellsPerBlock = FEC_REGION_CELLS;
+#ifndef FEC_REGION_TAIL_DIV
+#define FEC_REGION_TAIL_DIV 2
+#endif
+constexpr uint32_t kRegionTailDiv = FEC_REGION_TAIL_DIV;  // default split of the last regions
 constexpr int kRegionThreads = FEC_REGION_THREADS;
 constexpr int kRegionBlocksPerSM = FEC_REGION_BLOCKS;
 constexpr uint32_t kWaitCap = 1u << 22;  // default: spin iterations before a wait gives up
@@ -211,9 +215,12 @@ struct Params {
     uint32_t nf = 1;
     uint32_t ntiles = 0;
     uint32_t rows = 0;
-    // tunables: largest region of the neighbour step (cells, 64..1024) and
-    // the sub-cell size above which a warp, not a thread, reduces a sub-cell
+    // tunables: largest region of the neighbour step (cells, 32..1024), how
+    // many times smaller its last grid-full of regions is cut (its schedule),
+    // and the sub-cell size above which a warp, not a thread, reduces a
+    // sub-cell
     uint32_t region_cells = kRegionCellsPerBlock;
+    uint32_t region_tail = kRegionTailDiv;
     uint32_t big_subcell = kBigSubcell;
 };
 

@@ -381,13 +381,9 @@ __global__ void __launch_bounds__(256, 4)
 // Only boundary edges and cross-region pairs leave the block, through
 // shared-memory buffers flushed in chunks.
 // ---------------------------------------------------------------------------
-#ifndef FEC_REGION_TAIL_DIV
-#define FEC_REGION_TAIL_DIV 2
-#endif
 #ifndef FEC_REGION_TAIL_ROUNDS
 #define FEC_REGION_TAIL_ROUNDS 1
 #endif
-constexpr uint32_t kRegionTailDiv = FEC_REGION_TAIL_DIV;
 constexpr uint32_t kRegionTailRounds = FEC_REGION_TAIL_ROUNDS;
 constexpr int kRegionCells = (int)kRegionCellsPerBlock;
 constexpr int kRegionWarps = kRegionThreads / 32;
@@ -513,10 +509,10 @@ __global__ void __launch_bounds__(kRegionThreads, kRegionBlocksPerSM)
             // region size: kRegionCells, or fewer cells when the cloud has too
             // few cells to give every block two regions.  The last
             // kRegionTailRounds * grid full regions' worth of cells is cut into
-            // regions kRegionTailDiv times smaller, so that blocks finish together.
+            // regions prm.region_tail times smaller, so that blocks finish together.
             const uint32_t rc =
                 min(prm.region_cells, max(kRegionMinCells, M / (2u * gridDim.x)));
-            const uint32_t rt = max(kRegionMinCells, rc / kRegionTailDiv);
+            const uint32_t rt = max(kRegionMinCells, rc / max(prm.region_tail, 1u));
             const uint64_t tail = (uint64_t)kRegionTailRounds * gridDim.x * rc;
             const uint64_t full = M > tail ? (M - tail) / rc : 0;  // full-size regions
             const uint32_t r = atomicAdd(&plan->region_counter, 1u);

@@ -129,3 +129,33 @@ def test_batch_replays_and_shapes(ctx):
     for _ in range(2):
         _check(ctx, xs, d, [50] * 20, [50_000] * 20)
     _check(ctx, xs[:7], d[:7], [50] * 7, [50_000] * 7)
+
+
+def test_tuning_file_round_trip(tmp_path):
+    """The tuner writes one "key lanes region big tail" line per batch shape to the
+    context's cache file; a new context reading that file runs the same batch
+    with the stored configuration and gives the same labels."""
+    import torch
+
+    from paper_2208_07678_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(0)
+    frames = synth.batch_256(seed=11, n_frames=12, lo=2_000, hi=20_000)
+    xs = [f.xyz for f in frames]
+    d = [f.d for f in frames]
+    offs = np.zeros(len(xs) + 1, np.int64)
+    offs[1:] = np.cumsum([len(x) for x in xs])
+    xyz = np.concatenate(xs)
+    path = str(tmp_path / "tune.txt")
+    with fec.Context(device=0, autotune_cache=path) as c1:
+        lab1, k1 = c1.cluster_batch(xyz, offs, d, [20] * 12, [40_000] * 12)
+    lines = [l.split() for l in open(path).read().splitlines() if l.strip()]
+    assert lines and all(len(l) == 5 for l in lines)
+    for _, lanes, region, big, tail in lines:
+        assert 1 <= int(lanes) <= 8 and int(region) in (256, 512, 1024)
+        assert int(big) in (32, 64, 128) and int(tail) in (1, 2, 4)
+    with fec.Context(device=0, autotune_cache=path) as c2:
+        lab2, k2 = c2.cluster_batch(xyz, offs, d, [20] * 12, [40_000] * 12)
+    np.testing.assert_array_equal(np.asarray(lab1), np.asarray(lab2))
+    np.testing.assert_array_equal(np.asarray(k1), np.asarray(k2))
