@@ -102,6 +102,8 @@ void fec_destroy(fec_ctx *ctx);
  *   min_size, max_size  inclusive size bounds of kept clusters.
  *   labels       int32 [n], host or device memory, written in input order:
  *                0..k-1 by smallest point index, -1 for dropped points.
+ *                After any status other than FEC_OK its contents are
+ *                unspecified.
  *   num_clusters host int32: k, the number of kept clusters.
  * Synchronous: returns after labels and num_clusters are written.
  * Precedence of data errors: NONFINITE before OUT_OF_RANGE. */
