@@ -1,6 +1,6 @@
 """Host-side logic of bench.py (no GPU): clock-sample summaries, the guard on
-committed DRAM-traffic figures, the algorithmic-byte table and the bounded
-oracle sample."""
+committed DRAM-traffic figures, the algorithmic-byte table, the bounded
+oracle sample and the submit/poll loop of the pipelined end-to-end figure."""
 import importlib.util
 import json
 import os
@@ -122,3 +122,89 @@ def test_host_info_and_all_core_batch_baseline():
     frames = synth.batch_256(seed=8, n_frames=3, lo=500, hi=1_000)
     out = bench.time_oracle_batch(frames, processes=2)
     assert out["frames_per_s"] > 0 and out["cores"] == 2 and out["kind"] == "oracle"
+
+
+class _FakeBuffer:
+    _next = 0x1000
+
+    def __init__(self):
+        _FakeBuffer._next += 0x100
+        self.ptr = _FakeBuffer._next
+
+    def pin_memory(self):
+        return self
+
+    def data_ptr(self):
+        return self.ptr
+
+
+class _FakeTorch:
+    int32 = "int32"
+
+    @staticmethod
+    def empty(n, dtype=None):
+        return _FakeBuffer()
+
+    class cuda:
+        @staticmethod
+        def synchronize(dev=None):
+            pass
+
+
+class _FakeFec:
+    """Records the submit/poll sequence of the pipelined end-to-end loop."""
+    FEC_OK = 0
+    STATUS = {0: "FEC_OK"}
+
+    class FecError(RuntimeError):
+        def __init__(self, st, where=""):
+            super().__init__(where)
+
+    def __init__(self):
+        self.in_flight = {}   # ticket -> label buffer
+        self.max_in_flight = 0
+        self.events = []
+        self.next_ticket = 1
+        fake = self
+
+        class Context:
+            def __init__(self, device=0):
+                self.handle = 7
+
+            def __enter__(self):
+                return self
+
+            def __exit__(self, *a):
+                return False
+
+            def poll(self, t, timeout_ms=-1):
+                fake.events.append(("poll", t))
+                del fake.in_flight[t]
+                return 0, 42
+
+        self.Context = Context
+
+    def fec_serve_submit(self, handle, xyz, n, d, mn, mx, out):
+        assert out not in self.in_flight.values(), "a label buffer reused while its request is in flight"
+        t = self.next_ticket
+        self.next_ticket += 1
+        self.in_flight[t] = out
+        self.max_in_flight = max(self.max_in_flight, len(self.in_flight))
+        self.events.append(("submit", t))
+        return 0, t
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_pipelined_e2e_keeps_depth_in_flight_and_never_reuses_a_busy_buffer(bench, depth):
+    from types import SimpleNamespace
+
+    fake = _FakeFec()
+    cloud = SimpleNamespace(n=1000, d=0.2, min_size=1, max_size=10)
+    r = bench.measure_e2e_pipelined(fake, _FakeTorch, SimpleNamespace(index=0), cloud, _FakeBuffer(),
+                                    steps=7, warmup=3, depth=depth)
+    assert fake.max_in_flight == depth and not fake.in_flight
+    submits = [t for e, t in fake.events if e == "submit"]
+    polls = [t for e, t in fake.events if e == "poll"]
+    assert polls == submits  # every request completed, oldest first
+    assert r["h2d_bytes_per_step"] == 12 * 1000 and r["d2h_bytes_per_step"] == 4 * 1000 + 4
+    assert r["k"] == 42 and r["value"] > 0 and f"{depth} clouds in flight" in r["api"]
