@@ -266,7 +266,8 @@ __device__ __forceinline__ int quantize1(float x, int32_t &q)
 //   [ c0 >> B0 | c1 >> B1 | c0 mod 2^B0 | c1 mod 2^B1 | c2 ]
 // so that a run of consecutive cells (a region of the neighbour step) is a
 // compact block of columns instead of a one-cell-thick slice along p0: fewer
-// neighbour pairs cross regions.  A column's cells stay consecutive (c2 is
+// neighbour pairs cross regions.  (Host and device: a CPU test checks the
+// layout's round trips, tests/key_layout_main.cu.)  A column's cells stay consecutive (c2 is
 // the lowest field), and the "slab" of c0 is the key range of its brick row,
 // c0 >> B0.
 #ifndef FEC_KEY_BRICK
@@ -274,22 +275,22 @@ __device__ __forceinline__ int quantize1(float x, int32_t &q)
 #endif
 struct CellKeyLayout {
     uint32_t b0, b1, b2, B0, B1;
-    __device__ __forceinline__ void load(const Plan *plan)
+    __host__ __device__ __forceinline__ void load(const Plan *plan)
     {
         b0 = plan->bits[0];
         b1 = plan->bits[1];
         b2 = plan->bits[2];
-        B0 = min(b0, (uint32_t)FEC_KEY_BRICK);
-        B1 = min(b1, (uint32_t)FEC_KEY_BRICK);
+        B0 = b0 < (uint32_t)FEC_KEY_BRICK ? b0 : (uint32_t)FEC_KEY_BRICK;
+        B1 = b1 < (uint32_t)FEC_KEY_BRICK ? b1 : (uint32_t)FEC_KEY_BRICK;
     }
     // cell key of column (c0, c1) at c2 = 0
-    __device__ __forceinline__ unsigned long long column(unsigned long long c0, unsigned long long c1) const
+    __host__ __device__ __forceinline__ unsigned long long column(unsigned long long c0, unsigned long long c1) const
     {
         const unsigned long long m0 = (1ull << B0) - 1, m1 = (1ull << B1) - 1;
         return ((c0 >> B0) << (b2 + b1 + B0)) | ((c1 >> B1) << (b2 + B1 + B0)) | ((c0 & m0) << (b2 + B1)) |
                ((c1 & m1) << b2);
     }
-    __device__ __forceinline__ void decode(unsigned long long ck, unsigned long long &c0,
+    __host__ __device__ __forceinline__ void decode(unsigned long long ck, unsigned long long &c0,
                                            unsigned long long &c1, unsigned long long &c2) const
     {
         const unsigned long long m0 = (1ull << B0) - 1, m1 = (1ull << B1) - 1;
@@ -298,7 +299,7 @@ struct CellKeyLayout {
         c0 = ((ck >> (b2 + b1 + B0)) << B0) | ((ck >> (b2 + B1)) & m0);
     }
     // slab (brick row) of a major coordinate
-    __device__ __forceinline__ unsigned long long slab_of(unsigned long long c0) const { return c0 >> B0; }
+    __host__ __device__ __forceinline__ unsigned long long slab_of(unsigned long long c0) const { return c0 >> B0; }
 };
 
 // Grid coordinates of a quantised point under the plan.  The sort key is
@@ -314,7 +315,7 @@ struct GridMap {
     int32_t S, h;
     uint32_t div_m, div_s;  // floor(rel / S) == (rel * div_m) >> div_s for rel < 2^24
 
-    __device__ __forceinline__ void load(const Plan *plan, const Params &prm, const Frame &fr)
+    __host__ __device__ __forceinline__ void load(const Plan *plan, const Params &prm, const Frame &fr)
     {
         CellKeyLayout L;
         L.load(plan);
@@ -339,13 +340,13 @@ struct GridMap {
         div_s = prm.div_s;
     }
     // Another frame of the same call: only the grid origin changes.
-    __device__ __forceinline__ void set_frame(const Frame &fr)
+    __host__ __device__ __forceinline__ void set_frame(const Frame &fr)
     {
 #pragma unroll
         for (int a = 0; a < 3; ++a) lo[a] = fr.lo[a];
     }
     // Cell coordinate and offset inside the cell, per original axis.
-    __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
+    __host__ __device__ __forceinline__ void cell_of(const int32_t q[3], uint32_t c[3], uint32_t off[3]) const
     {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -356,7 +357,7 @@ struct GridMap {
     }
     // Sort key of a point (KeyT: uint32 when the key has at most 32 bits).
     template <typename KeyT>
-    __device__ __forceinline__ KeyT key_of(const uint32_t c[3], const uint32_t off[3]) const
+    __host__ __device__ __forceinline__ KeyT key_of(const uint32_t c[3], const uint32_t off[3]) const
     {
         KeyT k = 0;
 #pragma unroll
@@ -368,14 +369,14 @@ struct GridMap {
     // Sort payload of the packed layout: the original index in the low 32
     // bits and the point's offsets inside its cell (original axes x, y, z,
     // 10 bits each, S <= 1024) above it.
-    __device__ __forceinline__ unsigned long long payload_of(const uint32_t off[3], uint32_t idx) const
+    __host__ __device__ __forceinline__ unsigned long long payload_of(const uint32_t off[3], uint32_t idx) const
     {
         return (unsigned long long)idx | ((unsigned long long)off[0] << 32) |
                ((unsigned long long)off[1] << 42) | ((unsigned long long)off[2] << 52);
     }
     // Inverse of key_of() + payload_of(): the quantised coordinates of a point.
     template <typename KeyT>
-    __device__ __forceinline__ void unpack(KeyT key, unsigned long long v, int32_t q[3]) const
+    __host__ __device__ __forceinline__ void unpack(KeyT key, unsigned long long v, int32_t q[3]) const
     {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
